@@ -1,0 +1,499 @@
+#!/usr/bin/env python3
+"""Benchmark of the normal-variate hot path on GB300, one JSON line on stdout.
+
+A step is one pass over every row of the path on synthetic inputs:
+  B1    Box-Muller, N = 2^28 fp32, mu 0, sigma 1, key 0x5EED0001 (accurate)
+  P     Polar with order-preserving compaction, same parameters (accurate)
+  batch 4096 streams, lengths log-uniform in [1e2, 1e6] (seed 7), mixed B1/P,
+        mu ~ U(-2, 2), sigma ~ U(0.1, 3), one persistent launch in a CUDA graph
+  rep   reparameterised sample [1024, 8192]: forward x = mu + sigma z, upstream
+        gradient of sum(w x^2), backward (z regenerated from its counter)
+`value` is normals written per second over the whole step (all ranks).
+Every output is larger than L2 (129 MB), so no L2 flush is needed between
+steps.  `e2e` repeats the step through the same C-ABI calls with host
+buffers: the inputs are copied in from pinned host memory and every output is
+copied back, inside the timed region.
+
+--impl reference times the FP64 CPU oracle instead (a deliberately slow
+reference, on bounded samples of the same workload).
+
+Multi-GPU (torchrun): every rank runs an independent replica of the step on
+its own GPU with its own Philox counter range (the path needs no exchange);
+timing is the max over ranks between barriers.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KEY = 0x5EED0001
+N_FULL = 1 << 28
+PEAK_FALLBACK_GBS = 6800.0
+
+
+# ---------------------------------------------------------------- helpers --
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def rank_counter_base(rank: int, blocks_per_rank: int) -> int:
+    """First Philox block of a rank's replica: disjoint ranges per rank."""
+    return rank * blocks_per_rank
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return PEAK_FALLBACK_GBS, "fallback"
+
+
+def source_digest() -> str:
+    """Digest of the kernel sources, to tell whether recorded counters are stale."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1004_3105_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch recorded from an ncu capture of the current
+    sources (profiles/ncu_traffic.json), else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        rec = d.get(kernel)
+        if rec and rec.get("source_digest") == source_digest():
+            return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# --------------------------------------------------------------- clocks ----
+class ClockSampler:
+    """Samples SM clock, max clock and clock-event reasons through NVML (read
+    only) in a thread while the timed region runs."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown", 0x2: "applications_clocks_setting",
+               0x1: "gpu_idle"}
+
+    def __init__(self, cuda_index: int, period_s: float = 0.005):
+        self.samples, self.reasons, self.max_mhz = [], set(), None
+        self.period = period_s
+        self.ok = False
+        self._stop = threading.Event()
+        try:
+            self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            if not self._handle(cuda_index):
+                return
+            mx = ctypes.c_uint(0)
+            if self.nvml.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = int(mx.value)
+            self.ok = True
+        except OSError:
+            pass
+
+    def _handle(self, cuda_index: int) -> bool:
+        try:
+            import torch
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(cuda_index).uuid)
+            if self.nvml.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) == 0:
+                return True
+        except Exception:
+            pass
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        idx = cuda_index
+        parts = [v.strip() for v in vis.split(",") if v.strip()]
+        if parts and cuda_index < len(parts) and parts[cuda_index].isdigit():
+            idx = int(parts[cuda_index])
+        return self.nvml.nvmlDeviceGetHandleByIndex_v2(idx, ctypes.byref(self.h)) == 0
+
+    def _run(self):
+        clk = ctypes.c_uint(0)
+        rs = ctypes.c_ulonglong(0)
+        while not self._stop.is_set():
+            if self.nvml.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk)) == 0:
+                self.samples.append(int(clk.value))
+            if self.nvml.nvmlDeviceGetCurrentClocksEventReasons(self.h, ctypes.byref(rs)) == 0:
+                for bit, name in self.REASONS.items():
+                    if rs.value & bit and name != "gpu_idle":
+                        self.reasons.add(name)
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.ok:
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        if self.ok:
+            self._stop.set()
+            self._t.join()
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
+                    "samples": len(self.samples), "source": "nvml unavailable" if not self.ok else "nvml"}
+        return {"sm_mhz": float(np.median(self.samples)), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples), "source": "nvml"}
+
+
+# ------------------------------------------------------------ GPU workload --
+class Step:
+    """Buffers and launches of one step of the hot path on one GPU."""
+
+    def __init__(self, rank: int, host_io: bool = False):
+        import torch
+
+        import paper_1004_3105_gb300 as nr
+        from paper_1004_3105_gb300 import workloads as W
+        self.torch, self.nr, self.W = torch, nr, W
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = torch.cuda.current_stream()
+        # disjoint counter ranges per rank (replicas of the same workload)
+        self.base = rank_counter_base(rank, 1 << 40)
+        self.out_b1 = torch.empty(N_FULL, dtype=torch.float32, device=dev)
+        self.out_p = torch.empty(N_FULL, dtype=torch.float32, device=dev)
+        self.ws_p = nr.polar_workspace(N_FULL, dev)
+        wl = W.batched_workload(methods="mixed", align=4)
+        desc = nr.stream_descriptors(wl.offset, wl.n, wl.mu, wl.sigma, wl.key, wl.counter + np.uint64(self.base),
+                                     wl.method)
+        self.batch_total, self.batch_k = wl.total, len(desc)
+        self.desc_host = desc
+        self.desc_dev = nr.descriptors_to_device(desc, dev)
+        self.out_batch = torch.empty(wl.total, dtype=torch.float32, device=dev)
+        self.ws_batch = torch.empty(nr.nrng_batched_workspace_size(desc), dtype=torch.uint8, device=dev)
+        rw = W.reparam_workload()
+        self.rep_shape = W.REPARAM_SHAPE
+        self.mu = torch.from_numpy(rw.mu).to(dev)
+        self.sigma = torch.from_numpy(rw.sigma).to(dev)
+        self.w = torch.from_numpy(rw.w).to(dev)
+        self.x = torch.empty(self.rep_shape, dtype=torch.float32, device=dev)
+        self.g = torch.empty_like(self.x)
+        self.dmu = torch.empty_like(self.mu)
+        self.dsigma = torch.empty_like(self.sigma)
+        self.n_rep = int(np.prod(self.rep_shape))
+        # autotune the batched launch, then capture it in a graph
+        self.batch_cfg, _ = nr.nrng_batched_autotune(self.out_batch, self.desc_dev, self.batch_k, self.ws_batch,
+                                                     "accurate", reps=3)
+        self.graph = nr.BatchedGraph(self.out_batch, self.desc_dev, self.batch_k, self.ws_batch, "accurate")
+        self.host_io = host_io
+        if host_io:
+            pin = dict(dtype=torch.float32, pin_memory=True)
+            self.h_b1 = torch.empty(N_FULL, **pin)
+            self.h_p = torch.empty(N_FULL, **pin)
+            self.h_batch = torch.empty(wl.total, **pin)
+            self.h_x = torch.empty(self.rep_shape, **pin)
+            self.h_dmu = torch.empty(self.rep_shape, **pin)
+            self.h_dsigma = torch.empty(self.rep_shape, **pin)
+            self.h_mu = torch.from_numpy(rw.mu).pin_memory()
+            self.h_sigma = torch.from_numpy(rw.sigma).pin_memory()
+            self.h_w = torch.from_numpy(rw.w).pin_memory()
+            self.h_desc = torch.from_numpy(desc.view(np.uint8).copy()).pin_memory()
+        self.normals_per_step = 2 * N_FULL + self.batch_total + self.n_rep
+        # our kernels per step: B1 1, Polar 1, batched 2 (prep + main), reparam fwd + bwd 2
+        self.our_launches_per_step = 6
+
+    def part_b1(self):
+        self.nr.nrng_boxmuller(self.out_b1, 0.0, 1.0, KEY, self.base, "accurate")
+
+    def part_polar(self):
+        self.nr.nrng_polar(self.out_p, 0.0, 1.0, KEY, self.base, self.ws_p, "accurate")
+
+    def part_batch(self):
+        self.graph.launch()
+
+    def part_reparam(self):
+        nr = self.nr
+        nr.nrng_reparam_fwd(self.x, self.mu, self.sigma, KEY + 1, self.base, "accurate")
+        self.torch.mul(self.w, self.x, out=self.g)
+        self.g.mul_(2.0)
+        nr.nrng_reparam_bwd(self.dmu, self.dsigma, self.g, KEY + 1, self.base, "accurate")
+
+    PARTS = ("b1", "polar", "batch", "reparam")
+
+    def run_parts(self, events=None):
+        for i, name in enumerate(self.PARTS):
+            if events is not None:
+                events[i][0].record()
+            getattr(self, "part_" + name)()
+            if events is not None:
+                events[i][1].record()
+
+    def run_e2e(self):
+        """The step through host buffers: inputs in from pinned memory, every
+        output back to pinned memory."""
+        torch = self.torch
+        self.mu.copy_(self.h_mu.view(self.rep_shape), non_blocking=True)
+        self.sigma.copy_(self.h_sigma.view(self.rep_shape), non_blocking=True)
+        self.w.copy_(self.h_w.view(self.rep_shape), non_blocking=True)
+        self.desc_dev.copy_(self.h_desc, non_blocking=True)
+        self.part_b1()
+        self.h_b1.copy_(self.out_b1, non_blocking=True)
+        self.part_polar()
+        self.h_p.copy_(self.out_p, non_blocking=True)
+        self.part_batch()
+        self.h_batch.copy_(self.out_batch, non_blocking=True)
+        self.part_reparam()
+        self.h_x.copy_(self.x, non_blocking=True)
+        self.h_dmu.copy_(self.dmu, non_blocking=True)
+        self.h_dsigma.copy_(self.dsigma, non_blocking=True)
+
+    def e2e_bytes(self):
+        h2d = 3 * self.n_rep * 4 + self.h_desc.numel()
+        d2h = 4 * (2 * N_FULL + self.batch_total + 3 * self.n_rep)
+        return h2d, d2h
+
+    def check_status(self):
+        nr = self.nr
+        for ws in (self.ws_p, self.ws_batch):
+            st = nr.nrng_get_status(ws)
+            if st != 0:
+                raise RuntimeError(f"device status {nr._lib.STATUS.get(st, st)}")
+
+
+def cpu_oracle_sample(seconds_budget: float = 12.0):
+    """Times the FP64 oracle (single thread) on a bounded sample of the step's
+    mix: B1 and Polar at equal counts plus a slice of the batched streams and
+    of the reparameterised sample."""
+    import oracle
+    from paper_1004_3105_gb300 import workloads as W
+    oracle.build()
+    n = 1 << 21
+    t0 = time.perf_counter()
+    oracle.boxmuller(n, 0.0, 1.0, KEY, 0)
+    oracle.polar(n, 0.0, 1.0, KEY, 0)
+    wl = W.batched_workload(k=64, methods="mixed")
+    oracle.batched(wl.total, wl.as_dict())
+    rw = W.reparam_workload(shape=(64, 8192))
+    m = rw.mu.size
+    x = oracle.reparam_fwd(rw.mu, rw.sigma, m, 1, KEY + 1, 0)
+    oracle.reparam_bwd((2 * rw.w.ravel() * x).astype(np.float32), m, 1, KEY + 1, 0)
+    dt = time.perf_counter() - t0
+    normals = 2 * n + wl.total + m
+    scale = max(1, int(seconds_budget / max(dt, 1e-3)))
+    # repeat to fill the budget (bounded: at most ~seconds_budget of CPU work)
+    reps = min(scale, 8)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.boxmuller(n, 0.0, 1.0, KEY, 0)
+        oracle.polar(n, 0.0, 1.0, KEY, 0)
+        oracle.batched(wl.total, wl.as_dict())
+        x = oracle.reparam_fwd(rw.mu, rw.sigma, m, 1, KEY + 1, 0)
+        oracle.reparam_bwd((2 * rw.w.ravel() * x).astype(np.float32), m, 1, KEY + 1, 0)
+    dt = time.perf_counter() - t0
+    return {"value": reps * normals / dt, "unit": "normals/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x (B1 2^21 + Polar 2^21 + 64 batched streams ({wl.total} normals) + "
+                      f"reparam fwd+bwd [64, 8192]), FP64 single-threaded C oracle",
+            "seconds": round(dt, 2)}
+
+
+# ------------------------------------------------------------------- arms --
+def bench_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    n = 1 << 20
+    t_list = []
+
+    def step():
+        oracle.boxmuller(n, 0.0, 1.0, KEY, 0)
+        oracle.polar(n, 0.0, 1.0, KEY, 0)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = args.steps * 2 * n / dt
+    line = {
+        "impl": "reference", "metric": "normals/s", "value": value, "unit": "normals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "B1 + Polar normals, sample of 2^20 each per step (oracle), key 0x5EED0001",
+                   "sample_per_step": 2 * n},
+        "cpu_baseline": {"value": value, "unit": "normals/s", "cores": 1, "kind": "oracle",
+                         "sample": f"B1 2^20 + Polar 2^20 per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": "normals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_ours(args):
+    rank, world, local = dist_env()
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    import paper_1004_3105_gb300 as nr
+    nr.load()
+    step = Step(rank, host_io=not args.no_e2e)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    for _ in range(args.warmup):
+        step.run_parts()
+    torch.cuda.synchronize()
+    step.check_status()
+    K = args.steps
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in Step.PARTS] for _ in range(K)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        start.record()
+        for k in range(K):
+            step.run_parts(ev[k])
+        stop.record()
+        torch.cuda.synchronize()
+    barrier(world)
+    step.check_status()
+    ms_local = start.elapsed_time(stop)
+    ms = max_over_ranks(ms_local, world)
+    part_ms = {name: float(np.mean([ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(K)]))
+               for i, name in enumerate(Step.PARTS)}
+    value = world * K * step.normals_per_step / (ms * 1e-3)
+
+    # ---- end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ke = max(2, min(K, args.e2e_steps))
+        for _ in range(2):
+            step.run_e2e()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(Ke):
+            step.run_e2e()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier(world)
+        ems = max_over_ranks(e0.elapsed_time(e1), world)
+        h2d, d2h = step.e2e_bytes()
+        e2e = {"value": world * Ke * step.normals_per_step / (ems * 1e-3), "unit": "normals/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": Ke,
+               "ms_per_step": ems / Ke}
+
+    # ---- roofline of the dominant kernel and per-part rates
+    peak, peak_src = measured_peaks()
+    alg_bytes = {"b1": 4 * N_FULL, "polar": 4 * N_FULL, "batch": 4 * step.batch_total,
+                 "reparam": 24 * step.n_rep}   # fwd 12 B/elem; bwd reads g, writes dmu, dsigma: 12 B/elem
+    kernel_names = {"b1": "k_b1", "polar": "k_polar", "batch": "k_batched", "reparam": "k_reparam"}
+    parts = {}
+    for name in Step.PARTS:
+        t = part_ms[name] * 1e-3
+        gbs = alg_bytes[name] / t / 1e9
+        parts[name] = {"ms": round(part_ms[name], 4), "GB_per_s": round(gbs, 1),
+                       "frac_of_hbm": round(gbs / peak, 4)}
+    parts["b1"]["normals_per_s"] = N_FULL / (part_ms["b1"] * 1e-3)
+    parts["polar"]["normals_per_s"] = N_FULL / (part_ms["polar"] * 1e-3)
+    parts["batch"]["normals_per_s"] = step.batch_total / (part_ms["batch"] * 1e-3)
+    parts["batch"]["config"] = list(nr.nrng_batched_config_info(step.batch_cfg))
+    parts["reparam"]["fwd_bwd_per_s"] = 1.0 / (part_ms["reparam"] * 1e-3)
+    dom = max(("b1", "polar", "batch"), key=lambda nm: part_ms[nm])
+    t_dom = part_ms[dom] * 1e-3
+    achieved = alg_bytes[dom] / t_dom / 1e9
+    roofline = {"kernel": kernel_names[dom], "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                "traffic": recorded_traffic(kernel_names[dom]),
+                "algorithmic_bytes_per_launch": alg_bytes[dom]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": "normals/s", "value": value, "unit": "normals/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (Philox4x32-10 streams; seeded PCG64 inputs)",
+            "config": {"workload": "B1 2^28 fp32 + Polar 2^28 fp32 (accurate, mu 0, sigma 1, key 0x5EED0001) + "
+                                   "4096 batched streams (seed 7, mixed, graph) + reparam fwd+bwd [1024, 8192]",
+                       "N": N_FULL, "batched_normals": step.batch_total, "reparam_shape": list(step.rep_shape),
+                       "l2": "every output > L2 (1 GiB per single-stream kernel); no flush",
+                       "parallelism": f"replicas x{world}"},
+            "parts": parts, "roofline": roofline, "clocks": clocks.summary(),
+            "e2e": e2e, "gpu_launches": K * step.our_launches_per_step, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warmup raised to 3 (timing rule)")
+        args.warmup = 3
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * nrng.h -- C ABI of the GB300 (sm_103a) normal-variate library.
+ *
+ * Implements the bulk transformation of uniform variates into N(mu, sigma^2)
+ * variates of R. P. Brent, "Fast Normal Random Number Generators for Vector
+ * Processors" (TR-CS-93-04, 1993): Box-Muller Algorithm B1 and the Polar
+ * Algorithm P of Sec. 2, with P's rejection done as an order-preserving stream
+ * compaction (the vector compress/gather of Sec. 2 and Sec. 4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Uniform source.  The paper assumes a good generator of uniforms on [0, 1)
+ * that may return 0 but never 1 (Sec. 2, note a).  This library uses
+ * Philox4x32-10 (Salmon et al., SC'11).  Block b of a stream (key, counter)
+ * is Philox(ctr = (lo32(counter + b), hi32(counter + b), 0, 0),
+ * key = (lo32(key), hi32(key))) and yields four 32-bit words w0..w3.  A
+ * uniform is u = (w >> 8) * 2^-24, a point of the 24-bit dyadic lattice.
+ * The counter unit of every call is one Philox block (four words).
+ *
+ * Memory.  Every pointer named d_* is device memory owned by the caller; h_*
+ * is host memory.  The library never allocates device memory on these paths
+ * and keeps no pointer after a call returns.  Outputs need the natural
+ * alignment of their element type; wider alignment (16 bytes) selects the
+ * vector-store kernels, narrower alignment the element-store kernels.
+ *
+ * Streams.  Calls are asynchronous and stream-ordered on `stream` (a
+ * cudaStream_t; 0 is the legacy default stream).  A call returns after
+ * enqueueing its work.  Calls that take a workspace may not overlap on the
+ * GPU with another call using the same workspace.
+ *
+ * Errors.  Every call returns an nrng_status_t.  Errors the host can detect
+ * (a null pointer with n > 0, n < 0, sigma < 0 or not finite, mu not finite,
+ * an unknown enum, a misaligned pointer, a workspace that is too small, a
+ * Philox counter that would pass 2^64) return at once and enqueue nothing.
+ * A failed launch returns NRNG_ERR_CUDA.  Errors only the device can see
+ * (a look-back wait that ran out, a Polar stream that ran out of workspace
+ * tiles, a bad batched descriptor) are written to the workspace status word;
+ * read it with nrng_get_status.  n = 0 is a no-op that returns NRNG_OK.
+ */
+#ifndef NRNG_H
+#define NRNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Layout-compatible with cudaStream_t, so this header needs no CUDA header. */
+typedef struct CUstream_st *nrng_stream_t;
+
+typedef enum {
+    NRNG_OK = 0,
+    NRNG_ERR_INVALID_VALUE = 1,   /* bad size, pointer, parameter or enum */
+    NRNG_ERR_MISALIGNED = 2,      /* pointer not aligned to its element type */
+    NRNG_ERR_WORKSPACE = 3,       /* workspace missing or smaller than required */
+    NRNG_ERR_COUNTER_OVERFLOW = 4,/* counter + blocks used would pass 2^64 */
+    NRNG_ERR_CUDA = 5,            /* a CUDA runtime call or launch failed */
+    NRNG_ERR_TIMEOUT = 6,         /* device: a look-back wait ran out */
+    NRNG_ERR_EXHAUSTED = 7,       /* device: Polar needed more tiles than sized */
+    NRNG_ERR_NOT_SUPPORTED = 8    /* valid request this build does not handle */
+} nrng_status_t;
+
+typedef enum { NRNG_F32 = 0, NRNG_BF16 = 1, NRNG_F16 = 2 } nrng_dtype_t;
+
+/* NRNG_ACCURATE: log1pf/logf, sqrtf, IEEE division and sincospif.
+ * NRNG_FAST: the hardware approximations (__logf, sqrt.approx, __sincosf)
+ * with a short series for ln(1 - d) at small d, where the approximate log
+ * loses relative accuracy. */
+typedef enum { NRNG_ACCURATE = 0, NRNG_FAST = 1 } nrng_mode_t;
+
+typedef enum { NRNG_B1 = 0, NRNG_POLAR = 1 } nrng_method_t;
+
+/* One stream of a batched call: n normals of N(mu, sigma^2) drawn with
+ * `method` from (key, counter), written at element `offset` of the output. */
+typedef struct {
+    int64_t offset;
+    int64_t n;
+    float mu;
+    float sigma;
+    uint64_t key;
+    uint64_t counter;
+    int32_t method;     /* nrng_method_t */
+    int32_t reserved;   /* must be 0 */
+} nrng_stream_desc_t;
+
+/* Human-readable name of a status code (static storage). */
+const char *nrng_status_string(int32_t status);
+
+/* ABI version; bumps when any declaration in this header changes. */
+int32_t nrng_abi_version(void);
+
+/* Uniforms (paper Sec. 2: uniforms on [0, 1) that may be 0, never 1).
+ * d_out[i] = (w_{i mod 4} of block i/4) >> 8) * 2^-24 as float, exact.
+ * d_out: n floats, 4-byte aligned.  Uses ceil(n/4) blocks from `counter`. */
+int32_t nrng_uniform(float *d_out, int64_t n, uint64_t key, uint64_t counter,
+                     nrng_stream_t stream);
+
+/* Box-Muller, Algorithm B1 (paper Sec. 2, steps 1-3, notes a and b).
+ * Block b gives two pairs: (u, v) from words (w0, w1) and from (w2, w3).
+ * For each, r = sigma sqrt(-2 ln(1 - u)), x = r sin(2 pi v) + mu,
+ * y = r cos(2 pi v) + mu, stored at d_out[4b + 2p] (x) and [4b + 2p + 1] (y).
+ * d_out: n elements of `dtype` (fp32, or bf16/fp16 rounded to nearest even
+ * from the fp32 result).  Uses ceil(n/4) blocks from `counter`. */
+int32_t nrng_boxmuller(void *d_out, int64_t n, float mu, float sigma, uint64_t key,
+                       uint64_t counter, int32_t dtype, int32_t mode,
+                       nrng_stream_t stream);
+
+/* Workspace bytes nrng_polar needs for n outputs (tile status words, the
+ * tile counter and the status word).  Pure host computation. */
+int32_t nrng_polar_workspace_size(int64_t n, size_t *h_bytes);
+
+/* Largest number of Philox blocks nrng_polar may consume for n outputs
+ * (the workspace's tile budget); counter + this must not pass 2^64. */
+int32_t nrng_polar_max_blocks(int64_t n, uint64_t *h_blocks);
+
+/* Polar, Algorithm P (paper Sec. 2, steps 1-4), rejection as an
+ * order-preserving compaction (Sec. 2's vector gather, Sec. 4's compress).
+ * Candidate c (c = 0, 1, ...) is block counter + c/2, words 2(c mod 2) and
+ * 2(c mod 2) + 1: kx = (w >> 8) - 2^23, x = kx 2^-23 in [-1, 1), same for y.
+ * It is accepted iff 0 < S < 2^46 with S = kx^2 + ky^2 exact in 64-bit
+ * integers (s = S 2^-46 < 1, and s = 0 rejected).  The i-th accepted
+ * candidate gives d_out[2i] = r x + mu and d_out[2i + 1] = r y + mu with
+ * r = sigma sqrt(-2 ln(s) / s), for the first ceil(n/2) accepted candidates;
+ * an odd n drops the last y.
+ * d_ws/ws_bytes: workspace of at least nrng_polar_workspace_size(n) bytes,
+ *   cleared by this call; it holds the status word afterwards.
+ * d_next_counter (nullable): receives counter + c_last/2 + 1, the first block
+ *   with no consumed candidate, to continue the stream.
+ * d_pair_candidate (nullable): ceil(n/2) int64, the candidate index of each
+ *   output pair (for verification of the accept order).
+ * Device errors (NRNG_ERR_TIMEOUT, NRNG_ERR_EXHAUSTED) go to the status word. */
+int32_t nrng_polar(void *d_out, int64_t n, float mu, float sigma, uint64_t key,
+                   uint64_t counter, int32_t dtype, int32_t mode, void *d_ws,
+                   size_t ws_bytes, uint64_t *d_next_counter, int64_t *d_pair_candidate,
+                   nrng_stream_t stream);
+
+/* Workspace bytes nrng_batched needs for the k streams described in h_desc
+ * (host copy of the descriptors).  Pure host computation. */
+int32_t nrng_batched_workspace_size(const nrng_stream_desc_t *h_desc, int32_t k,
+                                    size_t *h_bytes);
+
+/* k independent streams in one persistent launch (B1 or Polar per stream, as
+ * nrng_boxmuller / nrng_polar define them, each at d_out + offset in elements
+ * of `dtype`).  d_desc: k descriptors in device memory.  Streams may not
+ * overlap in the output.  The per-stream work is scheduled as tiles pulled
+ * from one global work counter; Polar tiles look back within their stream.
+ * Descriptor errors found on the device (n < 0, sigma < 0, bad method, a
+ * workspace smaller than the descriptors need) set the status word and the
+ * launch writes nothing.  Capturable in a CUDA graph. */
+int32_t nrng_batched(void *d_out, const nrng_stream_desc_t *d_desc, int32_t k,
+                     int32_t dtype, int32_t mode, void *d_ws, size_t ws_bytes,
+                     nrng_stream_t stream);
+
+/* Reparameterised sample x = mu + sigma z (an add-on with no counterpart in
+ * the paper; z is the B1 stream of nrng_boxmuller with mu = 0, sigma = 1).
+ * Element i of x uses parameter p(i) = (i / inner) mod m of d_mu and
+ * d_sigma (m floats each): m = n is elementwise, m = 1 a scalar, any other
+ * m with inner a single broadcast axis; m * inner must divide n. */
+int32_t nrng_reparam_fwd(float *d_x, const float *d_mu, const float *d_sigma, int64_t n,
+                         int64_t m, int64_t inner, uint64_t key, uint64_t counter,
+                         int32_t mode, nrng_stream_t stream);
+
+/* Gradients of the reparameterised sample for upstream gradient d_g (n
+ * floats): d_dmu[p] = sum of g_i and d_dsigma[p] = sum of g_i z_i over the i
+ * with p(i) = p, z regenerated from (key, counter) instead of stored.
+ * d_dmu is nullable (skip it).  When m < n the sums use float atomics: their
+ * rounding order, not their terms, varies between runs. */
+int32_t nrng_reparam_bwd(float *d_dmu, float *d_dsigma, const float *d_g, int64_t n,
+                         int64_t m, int64_t inner, uint64_t key, uint64_t counter,
+                         int32_t mode, nrng_stream_t stream);
+
+/* Reads the status word a workspace call left behind (synchronises stream).
+ * Returns NRNG_OK on success of the read itself; *h_status is the word. */
+int32_t nrng_get_status(const void *d_ws, nrng_stream_t stream, int32_t *h_status);
+
+/* --------------------------------------------------------------------------
+ * Autotuning and graphs for the batched launch.
+ * -------------------------------------------------------------------------- */
+
+/* Number of compiled batched launch configurations and the shape of one:
+ * threads per CTA and Philox blocks each thread takes per tile. */
+int32_t nrng_batched_config_count(void);
+int32_t nrng_batched_config_info(int32_t config, int32_t *h_threads, int32_t *h_blocks_per_thread);
+
+/* Pins the configuration nrng_batched uses for (dtype, mode); -1 restores
+ * the default.  Thread-safe. */
+int32_t nrng_batched_set_config(int32_t dtype, int32_t mode, int32_t config);
+int32_t nrng_batched_get_config(int32_t dtype, int32_t mode, int32_t *h_config);
+
+/* Times every batched configuration on this workload (reps launches each,
+ * CUDA events on `stream`), pins the fastest for (dtype, mode) and returns it
+ * with its time in milliseconds per launch.  The workspace must be sized for
+ * the largest tile count of any configuration (nrng_batched_workspace_size
+ * already is).  If the environment variable NRNG_AUTOTUNE_CACHE names a file,
+ * the choice is appended to it as one JSON line.  Synchronises `stream`. */
+int32_t nrng_batched_autotune(void *d_out, const nrng_stream_desc_t *d_desc, int32_t k,
+                              int32_t dtype, int32_t mode, void *d_ws, size_t ws_bytes,
+                              int32_t reps, nrng_stream_t stream, int32_t *h_config,
+                              float *h_ms);
+
+/* Captures one nrng_batched call on `stream` (not the legacy default stream)
+ * into an instantiated CUDA graph; *h_graph receives an opaque handle. */
+int32_t nrng_batched_graph_create(void *d_out, const nrng_stream_desc_t *d_desc, int32_t k,
+                                  int32_t dtype, int32_t mode, void *d_ws, size_t ws_bytes,
+                                  nrng_stream_t stream, void **h_graph);
+int32_t nrng_graph_launch(void *h_graph, nrng_stream_t stream);
+int32_t nrng_graph_destroy(void *h_graph);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRNG_H */

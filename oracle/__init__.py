@@ -146,11 +146,12 @@ def polar(n: int, mu: float, sigma: float, key: int, counter: int):
     return out, cand, int(nxt[0]), int(ncand)
 
 
-def polar_candidates(ncand: int, key: int, counter: int):
-    """(accept[ncand] uint8, kx'[ncand], ky'[ncand]) for candidates 0 .. ncand-1."""
+def polar_candidates(ncand: int, key: int, counter: int, coords: bool = True):
+    """(accept[ncand] uint8, kx'[ncand], ky'[ncand]) for candidates 0 .. ncand-1
+    (kx', ky' are None when coords is False)."""
     acc = np.zeros(ncand, dtype=np.uint8)
-    kx = np.zeros(ncand, dtype=np.int32)
-    ky = np.zeros(ncand, dtype=np.int32)
+    kx = np.zeros(ncand, dtype=np.int32) if coords else None
+    ky = np.zeros(ncand, dtype=np.int32) if coords else None
     _load().orc_polar_candidates(_ptr(acc), _ptr(kx), _ptr(ky), ncand, _u64(key), _u64(counter))
     return acc, kx, ky
 

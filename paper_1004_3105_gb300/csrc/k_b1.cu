@@ -1,0 +1,121 @@
+// k_b1.cu -- uniforms and Box-Muller Algorithm B1 (paper Sec. 2, steps 1-3).
+//
+// One thread takes one Philox block at a time (grid-stride): four 32-bit
+// words give two (u, v) pairs and four outputs, stored with one 16-byte
+// (fp32) or 8-byte (bf16/fp16) streaming store.  There are no loads: the
+// kernel is bound by the HBM write stream or by the Philox + transform
+// instruction issue, whichever is tighter.
+#include <algorithm>
+
+#include "nrng_device.cuh"
+
+namespace nrng {
+
+constexpr int kB1Threads = 256;
+
+template <bool ALIGNED>
+__global__ void __launch_bounds__(kB1Threads)
+k_uniform(float *__restrict__ out, int64_t n, int64_t nblocks, uint64_t counter, const RoundKeys rk)
+{
+    const int64_t stride = (int64_t)gridDim.x * kB1Threads;
+    for (int64_t b = (int64_t)blockIdx.x * kB1Threads + threadIdx.x; b < nblocks; b += stride) {
+        const uint4 w = philox_block(counter + (uint64_t)b, rk);
+        const float a = u24(w.x), c = u24(w.y), d = u24(w.z), e = u24(w.w);
+        const int64_t i = 4 * b;
+        if (ALIGNED && i + 4 <= n) {
+            store4_aligned(out + i, a, c, d, e);
+        } else {
+            if (i < n) out[i] = a;
+            if (i + 1 < n) out[i + 1] = c;
+            if (i + 2 < n) out[i + 2] = d;
+            if (i + 3 < n) out[i + 3] = e;
+        }
+    }
+}
+
+template <int MODE, typename T, bool ALIGNED>
+__global__ void __launch_bounds__(kB1Threads)
+k_b1(T *__restrict__ out, int64_t n, int64_t nblocks, float mu, float sigma, uint64_t counter,
+     const RoundKeys rk)
+{
+    const int64_t stride = (int64_t)gridDim.x * kB1Threads;
+    for (int64_t b = (int64_t)blockIdx.x * kB1Threads + threadIdx.x; b < nblocks; b += stride) {
+        const uint4 w = philox_block(counter + (uint64_t)b, rk);
+        float x0, y0, x1, y1;
+        b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
+        b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
+        const int64_t i = 4 * b;
+        if (ALIGNED && i + 4 <= n) {
+            store4_aligned(out + i, x0, y0, x1, y1);
+        } else {
+            if (i < n) store1(out + i, x0);
+            if (i + 1 < n) store1(out + i + 1, y0);
+            if (i + 2 < n) store1(out + i + 2, x1);
+            if (i + 3 < n) store1(out + i + 3, y1);
+        }
+    }
+}
+
+// Grid: enough CTAs to fill every SM at full occupancy, grid-striding over
+// the blocks beyond that (the kernel holds no state between blocks).
+static int b1_grid(int64_t nblocks)
+{
+    const int64_t ctas = (nblocks + kB1Threads - 1) / kB1Threads;
+    const int64_t resident = (int64_t)sm_count() * (2048 / kB1Threads);
+    return (int)std::max<int64_t>(1, std::min(ctas, resident));
+}
+
+cudaError_t launch_uniform(float *out, int64_t n, uint64_t key, uint64_t counter, cudaStream_t s)
+{
+    const int64_t nblocks = (n + 3) / 4;
+    const RoundKeys rk = round_keys(key);
+    const bool aligned = ((uintptr_t)out % 16) == 0;
+    if (aligned)
+        k_uniform<true><<<b1_grid(nblocks), kB1Threads, 0, s>>>(out, n, nblocks, counter, rk);
+    else
+        k_uniform<false><<<b1_grid(nblocks), kB1Threads, 0, s>>>(out, n, nblocks, counter, rk);
+    return cudaGetLastError();
+}
+
+template <int MODE, typename T>
+static void b1_dispatch_aligned(void *out, int64_t n, int64_t nblocks, float mu, float sigma,
+                                uint64_t counter, const RoundKeys &rk, bool aligned, cudaStream_t s)
+{
+    const int grid = b1_grid(nblocks);
+    if (aligned)
+        k_b1<MODE, T, true><<<grid, kB1Threads, 0, s>>>((T *)out, n, nblocks, mu, sigma, counter, rk);
+    else
+        k_b1<MODE, T, false><<<grid, kB1Threads, 0, s>>>((T *)out, n, nblocks, mu, sigma, counter, rk);
+}
+
+template <int MODE>
+static void b1_dispatch_dtype(void *out, int64_t n, int64_t nblocks, float mu, float sigma,
+                              uint64_t counter, const RoundKeys &rk, int dtype, bool aligned,
+                              cudaStream_t s)
+{
+    switch (dtype) {
+    case NRNG_F32:
+        b1_dispatch_aligned<MODE, float>(out, n, nblocks, mu, sigma, counter, rk, aligned, s);
+        break;
+    case NRNG_BF16:
+        b1_dispatch_aligned<MODE, __nv_bfloat16>(out, n, nblocks, mu, sigma, counter, rk, aligned, s);
+        break;
+    default:
+        b1_dispatch_aligned<MODE, __half>(out, n, nblocks, mu, sigma, counter, rk, aligned, s);
+        break;
+    }
+}
+
+cudaError_t launch_b1(void *out, int64_t n, float mu, float sigma, uint64_t key, uint64_t counter,
+                      int dtype, int mode, bool aligned, cudaStream_t s)
+{
+    const int64_t nblocks = (n + 3) / 4;
+    const RoundKeys rk = round_keys(key);
+    if (mode == kModeFast)
+        b1_dispatch_dtype<kModeFast>(out, n, nblocks, mu, sigma, counter, rk, dtype, aligned, s);
+    else
+        b1_dispatch_dtype<kModeAccurate>(out, n, nblocks, mu, sigma, counter, rk, dtype, aligned, s);
+    return cudaGetLastError();
+}
+
+}  // namespace nrng

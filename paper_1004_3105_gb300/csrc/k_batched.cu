@@ -1,0 +1,298 @@
+// k_batched.cu -- many independent streams (each B1 or Polar, each with its
+// own mu, sigma, key, counter and length) in one persistent launch.
+//
+// The paper amortises the cost of a call by returning whole arrays (Sec. 3)
+// and buffers the variable output of its vector Polar kernel (Sec. 4,
+// RANN3/RANN3B).  Here thousands of uneven streams share one grid:
+//   k_batched_prep (one CTA) validates the descriptors, turns each stream into
+//     a number of tiles (its work items) and scans them, together with the
+//     Polar streams' tile status slots, into the workspace;
+//   k_batched (persistent, one global work counter) pulls items in order,
+//     finds the stream by binary search over the item prefix and runs one B1
+//     tile or one Polar tile (look-back within the stream's own status words).
+// Items of one stream are consecutive and handed out in increasing order, so
+// a Polar tile only waits on tiles already owned by running CTAs.  A Polar
+// tile taken after its stream is complete publishes a prefix of npairs and
+// returns, so that any later tile's look-back still terminates.
+#include <algorithm>
+#include <climits>
+
+#include "tiles.cuh"
+
+namespace nrng {
+
+// ------------------------------------------------------------ configs -----
+// (threads per CTA, Philox blocks per thread per tile); the Polar staging
+// buffer of the largest is 2 * 256 * 8 candidates * 10 bytes = 40 KB.
+static const BatchedConfig kConfigs[] = {
+    {256, 2}, {256, 4}, {256, 8}, {128, 4}, {128, 8}, {512, 2},
+};
+constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
+
+int batched_config_count() { return kNumConfigs; }
+BatchedConfig batched_config(int id) { return kConfigs[id]; }
+int batched_default_config() { return 1; }
+
+__host__ __device__ inline int64_t b1_items(int64_t n, int64_t tile_blocks)
+{
+    const int64_t nblocks = (n + 3) / 4;
+    return (nblocks + tile_blocks - 1) / tile_blocks;
+}
+
+// Items and status slots of one stream; -1 items marks an invalid descriptor.
+__host__ __device__ inline void stream_items(const nrng_stream_desc_t &d, int threads, int bpt,
+                                             int64_t &items, int64_t &slots)
+{
+    items = 0;
+    slots = 0;
+    const bool finite = (d.mu - d.mu == 0.0f) && (d.sigma - d.sigma == 0.0f);
+    if (d.n < 0 || d.offset < 0 || !finite || !(d.sigma >= 0.0f) || d.reserved != 0 ||
+        (d.method != NRNG_B1 && d.method != NRNG_POLAR) || (d.method == NRNG_POLAR && d.n > kPolarMaxN)) {
+        items = -1;
+        return;
+    }
+    if (d.n == 0) return;
+    const int64_t tile_blocks = (int64_t)threads * bpt;
+    if (d.method == NRNG_B1) {
+        items = b1_items(d.n, tile_blocks);
+        const uint64_t blocks = (uint64_t)((d.n + 3) / 4);
+        if (d.counter > ULLONG_MAX - (blocks - 1)) items = -2;
+    } else {
+        items = polar_tiles_for(d.n, 2 * tile_blocks);
+        slots = items;
+        const uint64_t blocks = (uint64_t)(items * tile_blocks);
+        if (d.counter > ULLONG_MAX - (blocks - 1)) items = -2;
+    }
+}
+
+size_t batched_workspace_bytes(const nrng_stream_desc_t *h_desc, int32_t k)
+{
+    // Sized for the configuration with the most status slots, so that any
+    // configuration (autotuned or pinned) fits the same workspace.
+    size_t best = 0;
+    for (int c = 0; c < kNumConfigs; ++c) {
+        int64_t slots = 0;
+        for (int32_t j = 0; j < k; ++j) {
+            int64_t it, sl;
+            stream_items(h_desc[j], kConfigs[c].threads, kConfigs[c].blocks_per_thread, it, sl);
+            if (it > 0) slots += sl;
+        }
+        best = std::max(best, (size_t)slots);
+    }
+    return batched_layout(k).tile_status + best * sizeof(unsigned long long);
+}
+
+// ------------------------------------------------------------ prep --------
+constexpr int kPrepThreads = 1024;
+
+__global__ void __launch_bounds__(kPrepThreads)
+k_batched_prep(BatchedParams bp, int threads, int bpt)
+{
+    __shared__ long long s_wi[kPrepThreads / 32], s_ws[kPrepThreads / 32];
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    long long carry_i = 0, carry_s = 0;
+    for (int32_t c0 = 0; c0 < bp.k; c0 += kPrepThreads) {
+        const int32_t j = c0 + tid;
+        int64_t items = 0, slots = 0;
+        if (j < bp.k) {
+            stream_items(bp.desc[j], threads, bpt, items, slots);
+            if (items < 0) {
+                atomicMax(&s_bad, items == -2 ? kStatusOverflow : kStatusInvalid);
+                items = 0;
+                slots = 0;
+            }
+        }
+        // block-wide exclusive scan of (items, slots)
+        long long ii = items, is = slots;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long a = __shfl_up_sync(0xFFFFFFFFu, ii, o);
+            const long long b = __shfl_up_sync(0xFFFFFFFFu, is, o);
+            if (lane >= o) { ii += a; is += b; }
+        }
+        if (lane == 31) { s_wi[warp] = ii; s_ws[warp] = is; }
+        __syncthreads();
+        if (warp == 0) {
+            long long wi = s_wi[lane], ws = s_ws[lane];
+            const long long wi0 = wi, ws0 = ws;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long a = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+                const long long b = __shfl_up_sync(0xFFFFFFFFu, ws, o);
+                if (lane >= o) { wi += a; ws += b; }
+            }
+            s_wi[lane] = wi - wi0;
+            s_ws[lane] = ws - ws0;
+        }
+        __syncthreads();
+        if (j < bp.k) {
+            bp.item_prefix[j] = carry_i + s_wi[warp] + ii - items;
+            bp.slot_base[j] = carry_s + s_ws[warp] + is - slots;
+        }
+        // chunk totals: the last thread's inclusive values
+        __shared__ long long s_ti, s_ts;
+        if (tid == kPrepThreads - 1) { s_ti = s_wi[warp] + ii; s_ts = s_ws[warp] + is; }
+        __syncthreads();
+        carry_i += s_ti;
+        carry_s += s_ts;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        bp.item_prefix[bp.k] = carry_i;
+        const size_t need = batched_layout(bp.k).tile_status + (size_t)carry_s * 8;
+        int bad = s_bad;
+        if (!bad && need > bp.ws_bytes) bad = kStatusWorkspace;
+        if (bad) {
+            bp.hdr->status = bad;
+            bp.hdr->done = 1;
+            bp.hdr->aux[0] = 0;
+        } else {
+            bp.hdr->aux[0] = (unsigned long long)carry_i;
+        }
+    }
+}
+
+// ------------------------------------------------------------ main --------
+template <int THREADS, int BPT, int MODE, typename T>
+__global__ void __launch_bounds__(THREADS)
+k_batched(BatchedParams bp)
+{
+    __shared__ PolarSmem<THREADS, BPT> sm;
+    __shared__ long long s_item;
+    __shared__ int s_stream;
+    __shared__ nrng_stream_desc_t s_desc;
+
+    const unsigned long long total_items = bp.hdr->aux[0];
+    char *out_base = static_cast<char *>(bp.out);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            long long item = -1;
+            if (ld_relaxed_s32(&bp.hdr->done) == 0) {
+                const unsigned long long it = atomicAdd(&bp.hdr->tile_counter, 1ull);
+                if (it < total_items) item = (long long)it;
+            }
+            int j = -1;
+            if (item >= 0) {
+                // largest j with item_prefix[j] <= item (streams with no items
+                // share their prefix with the next stream; take the last)
+                int lo = 0, hi = bp.k;   // item_prefix[lo] <= item < item_prefix[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) / 2;
+                    if (bp.item_prefix[mid] <= item) lo = mid; else hi = mid;
+                }
+                j = lo;
+                s_desc = bp.desc[j];
+            }
+            s_item = item;
+            s_stream = j;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item < 0) break;
+        const int j = s_stream;
+        const nrng_stream_desc_t d = s_desc;
+        const int64_t t = item - bp.item_prefix[j];
+        RoundKeys rk;
+        make_round_keys(d.key, rk);
+        T *out = reinterpret_cast<T *>(out_base) + d.offset;
+        bool ok = true;
+        if (d.method == NRNG_B1) {
+            if (((uintptr_t)out % (4 * sizeof(T))) == 0)
+                b1_tile<THREADS, BPT, MODE, T, true>(out, d.n, d.mu, d.sigma, rk, d.counter, t);
+            else
+                b1_tile<THREADS, BPT, MODE, T, false>(out, d.n, d.mu, d.sigma, rk, d.counter, t);
+        } else {
+            PolarStream ps;
+            ps.n = d.n;
+            ps.npairs = (d.n + 1) / 2;
+            ps.mu = d.mu;
+            ps.sigma = d.sigma;
+            ps.counter = d.counter;
+            ps.status = bp.tile_status + bp.slot_base[j];
+            ps.tiles_max = polar_tiles_for(d.n, 2 * THREADS * BPT);
+            ps.done = bp.stream_done + j;
+            ps.next_counter = nullptr;
+            ps.pair_cand = nullptr;
+            ps.silent_tile = -1;
+            if (ld_relaxed_s32(ps.done) != 0) {
+                // Stream complete: every later tile's prefix is >= npairs.
+                if (threadIdx.x == 0)
+                    st_relaxed(ps.status + t, kFlagPrefix | (unsigned long long)ps.npairs);
+            } else if (((uintptr_t)out % (2 * sizeof(T))) == 0) {
+                ok = polar_tile<THREADS, BPT, MODE, T, true>(sm, out, ps, rk, t, bp.hdr, bp.spin_limit_ns);
+            } else {
+                ok = polar_tile<THREADS, BPT, MODE, T, false>(sm, out, ps, rk, t, bp.hdr, bp.spin_limit_ns);
+            }
+        }
+        __syncthreads();
+        if (!ok) break;
+    }
+}
+
+template <int THREADS, int BPT, int MODE, typename T>
+static cudaError_t batched_main(const BatchedParams &bp, cudaStream_t s)
+{
+    static int occ = 0;
+    if (occ == 0) {
+        int o = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batched<THREADS, BPT, MODE, T>, THREADS, 0);
+        if (e != cudaSuccess) return e;
+        occ = std::max(o, 1);
+    }
+    k_batched<THREADS, BPT, MODE, T><<<sm_count() * occ, THREADS, 0, s>>>(bp);
+    return cudaGetLastError();
+}
+
+template <int MODE, typename T>
+static cudaError_t batched_config_dispatch(const BatchedParams &bp, int config, cudaStream_t s)
+{
+    switch (config) {
+    case 0: return batched_main<256, 2, MODE, T>(bp, s);
+    case 1: return batched_main<256, 4, MODE, T>(bp, s);
+    case 2: return batched_main<256, 8, MODE, T>(bp, s);
+    case 3: return batched_main<128, 4, MODE, T>(bp, s);
+    case 4: return batched_main<128, 8, MODE, T>(bp, s);
+    default: return batched_main<512, 2, MODE, T>(bp, s);
+    }
+}
+
+template <int MODE>
+static cudaError_t batched_dtype_dispatch(const BatchedParams &bp, int dtype, int config, cudaStream_t s)
+{
+    switch (dtype) {
+    case NRNG_F32: return batched_config_dispatch<MODE, float>(bp, config, s);
+    case NRNG_BF16: return batched_config_dispatch<MODE, __nv_bfloat16>(bp, config, s);
+    default: return batched_config_dispatch<MODE, __half>(bp, config, s);
+    }
+}
+
+cudaError_t launch_batched(void *out, const nrng_stream_desc_t *desc, int32_t k, int dtype, int mode,
+                           void *ws, size_t ws_bytes, int config, cudaStream_t s)
+{
+    const BatchedLayout L = batched_layout(k);
+    char *w = static_cast<char *>(ws);
+    BatchedParams bp;
+    bp.out = out;
+    bp.desc = desc;
+    bp.k = k;
+    bp.hdr = reinterpret_cast<WsHeader *>(w);
+    bp.item_prefix = reinterpret_cast<int64_t *>(w + L.item_prefix);
+    bp.slot_base = reinterpret_cast<int64_t *>(w + L.slot_base);
+    bp.stream_done = reinterpret_cast<int *>(w + L.stream_done);
+    bp.tile_status = reinterpret_cast<unsigned long long *>(w + L.tile_status);
+    bp.ws_bytes = ws_bytes;
+    bp.spin_limit_ns = spin_limit_ns();
+    cudaError_t e = cudaMemsetAsync(ws, 0, ws_bytes, s);
+    if (e != cudaSuccess) return e;
+    const BatchedConfig c = kConfigs[config];
+    k_batched_prep<<<1, kPrepThreads, 0, s>>>(bp, c.threads, c.blocks_per_thread);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (mode == kModeFast) return batched_dtype_dispatch<kModeFast>(bp, dtype, config, s);
+    return batched_dtype_dispatch<kModeAccurate>(bp, dtype, config, s);
+}
+
+}  // namespace nrng

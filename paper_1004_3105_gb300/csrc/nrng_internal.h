@@ -1,0 +1,157 @@
+// nrng_internal.h -- declarations shared by the host C-ABI layer and the
+// kernels: launch parameter blocks, workspace layouts and launchers.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "nrng.h"
+
+namespace nrng {
+
+constexpr int kModeAccurate = NRNG_ACCURATE;
+constexpr int kModeFast = NRNG_FAST;
+constexpr int kStatusTimeout = NRNG_ERR_TIMEOUT;
+constexpr int kStatusExhausted = NRNG_ERR_EXHAUSTED;
+constexpr int kStatusInvalid = NRNG_ERR_INVALID_VALUE;
+constexpr int kStatusWorkspace = NRNG_ERR_WORKSPACE;
+constexpr int kStatusOverflow = NRNG_ERR_COUNTER_OVERFLOW;
+
+// Philox round keys (key + r * Weyl increment, r = 0..9), computed once on
+// the host so that every round's key xor reads a constant-bank operand.
+struct RoundKeys {
+    uint32_t k0[10];
+    uint32_t k1[10];
+};
+RoundKeys round_keys(uint64_t key);
+
+// Header at the start of every workspace.  `status` is the word
+// nrng_get_status reads; `done` stops CTAs from taking further tiles.
+struct WsHeader {
+    int status;
+    int done;
+    unsigned long long tile_counter;
+    unsigned long long aux[6];
+};
+static_assert(sizeof(WsHeader) == 64, "workspace header is 64 bytes");
+
+// ---------------------------------------------------------------- Polar --
+constexpr int kPolarThreads = 256;
+constexpr int kPolarRows = 4;                                  // Philox blocks per thread per tile
+constexpr int kPolarBlocksPerTile = kPolarThreads * kPolarRows; // 1024
+constexpr int kPolarCandPerTile = 2 * kPolarBlocksPerTile;      // 2048
+
+struct PolarParams {
+    void *out;
+    int64_t n;
+    int64_t npairs;
+    float mu, sigma;
+    RoundKeys rk;
+    uint64_t counter;
+    WsHeader *hdr;
+    unsigned long long *tile_status;
+    int64_t tiles_max;
+    uint64_t *next_counter;
+    int64_t *pair_cand;
+    unsigned long long spin_limit_ns;
+    long long debug_silent_tile;   // test hook: this tile never publishes (-1: none)
+};
+
+// Largest n a Polar stream accepts (keeps the tile budget arithmetic exact).
+constexpr int64_t kPolarMaxN = int64_t(1) << 48;
+
+// floor(sqrt(v)) for 0 <= v < 2^62, exact, in integers only.
+__host__ __device__ inline int64_t isqrt64(int64_t v)
+{
+    int64_t lo = 0, hi = int64_t(1) << 31;   // hi * hi > v
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) / 2;
+        if (mid * mid <= v) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Tile budget of a Polar stream of n outputs in tiles of `cand` candidates:
+// enough candidates that running out is a > 12-sigma binomial event (the
+// acceptance probability is pi/4 = 0.7854; the budget assumes 0.78), plus
+// one spare tile.  Integer-only, so host sizing and device checks agree.
+__host__ __device__ inline int64_t polar_tiles_for(int64_t n, int64_t cand)
+{
+    const int64_t npairs = (n + 1) / 2;
+    const int64_t need = npairs + 12 * (isqrt64(npairs) + 1) + 16;
+    return (need * 100 + cand * 78 - 1) / (cand * 78) + 1;
+}
+
+int64_t polar_tiles_max(int64_t n);
+size_t polar_workspace_bytes(int64_t n);
+
+// ------------------------------------------------------------- launchers --
+cudaError_t launch_uniform(float *out, int64_t n, uint64_t key, uint64_t counter, cudaStream_t s);
+cudaError_t launch_b1(void *out, int64_t n, float mu, float sigma, uint64_t key, uint64_t counter,
+                      int dtype, int mode, bool aligned, cudaStream_t s);
+cudaError_t launch_polar(const PolarParams &p, int dtype, int mode, bool aligned, cudaStream_t s);
+cudaError_t launch_set_u64(uint64_t *p, uint64_t v, cudaStream_t s);
+
+// ---------------------------------------------------------------- reparam
+cudaError_t launch_reparam_fwd(float *x, const float *mu, const float *sigma, int64_t n, int64_t m,
+                               int64_t inner, uint64_t key, uint64_t counter, int mode, cudaStream_t s);
+cudaError_t launch_reparam_bwd(float *dmu, float *dsigma, const float *g, int64_t n, int64_t m,
+                               int64_t inner, uint64_t key, uint64_t counter, int mode, cudaStream_t s);
+
+// ---------------------------------------------------------------- batched
+struct BatchedConfig {
+    int threads;
+    int blocks_per_thread;
+};
+
+// Workspace of a batched call: header, then per-stream tables, then one tile
+// status word per Polar tile of every Polar stream.
+struct BatchedLayout {
+    size_t item_prefix;   // int64[k + 1]: first work item of each stream
+    size_t slot_base;     // int64[k]: first tile status word of each Polar stream
+    size_t stream_done;   // int32[k]: set once a Polar stream has all its pairs
+    size_t tile_status;   // uint64[slots]
+};
+__host__ __device__ inline BatchedLayout batched_layout(int32_t k)
+{
+    BatchedLayout L;
+    L.item_prefix = sizeof(WsHeader);
+    L.slot_base = L.item_prefix + (size_t)(k + 1) * 8;
+    L.stream_done = L.slot_base + (size_t)k * 8;
+    L.tile_status = (L.stream_done + (size_t)k * 4 + 255) / 256 * 256;
+    return L;
+}
+
+struct BatchedParams {
+    void *out;
+    const nrng_stream_desc_t *desc;
+    int32_t k;
+    WsHeader *hdr;
+    int64_t *item_prefix;
+    int64_t *slot_base;
+    int *stream_done;
+    unsigned long long *tile_status;
+    size_t ws_bytes;
+    unsigned long long spin_limit_ns;
+};
+int batched_config_count();
+BatchedConfig batched_config(int id);
+int batched_default_config();
+size_t batched_workspace_bytes(const nrng_stream_desc_t *h_desc, int32_t k);
+cudaError_t launch_batched(void *out, const nrng_stream_desc_t *desc, int32_t k, int dtype, int mode,
+                           void *ws, size_t ws_bytes, int config, cudaStream_t s);
+
+// Test hooks read from the environment at each call (both off by default):
+// NRNG_DEBUG_SILENT_TILE=t makes Polar tile t skip publishing its status, so
+// that its successors' bounded look-back waits run out (NRNG_ERR_TIMEOUT);
+// NRNG_DEBUG_POLAR_TILES=k caps a Polar call's tile budget at k tiles, so
+// that a large n runs out of tiles (NRNG_ERR_EXHAUSTED).
+long long debug_silent_tile();
+int64_t debug_polar_tiles();
+
+// Device properties cached per device.
+int sm_count();
+unsigned long long spin_limit_ns();
+
+}  // namespace nrng

@@ -1,0 +1,160 @@
+"""The C ABI without a GPU: libnrng.so loads, exports every function that
+include/nrng.h declares, and its host-side validation returns the documented
+status before anything is enqueued (only fake, never-dereferenced pointers
+are passed, and only to calls that reject them on the host)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1004_3105_gb300 import _lib
+from paper_1004_3105_gb300.nrng import STREAM_DESC
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "nrng.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _lib.load(build_if_missing=True)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nrng_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"binding lacks {name}"
+    assert lib.nrng_abi_version() == 1
+
+
+def test_status_strings(lib):
+    for code, name in _lib.STATUS.items():
+        assert lib.nrng_status_string(code).decode().startswith(name)
+    assert lib.nrng_status_string(99).decode() == "NRNG_ERR_UNKNOWN"
+
+
+FAKE = ctypes.c_void_p(0x100000)       # 256-byte aligned, never dereferenced
+ODD = ctypes.c_void_p(0x100001)
+
+
+def test_boxmuller_validation(lib):
+    f = lib.nrng_boxmuller
+    assert f(None, -1, 0.0, 1.0, 1, 0, 0, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(None, 5, 0.0, 1.0, 1, 0, 0, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, 5, 0.0, -1.0, 1, 0, 0, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, 5, float("nan"), 1.0, 1, 0, 0, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, 5, 0.0, float("inf"), 1, 0, 0, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, 5, 0.0, 1.0, 1, 0, 3, 0, None) == _lib.ERR_INVALID_VALUE      # dtype
+    assert f(FAKE, 5, 0.0, 1.0, 1, 0, 0, 2, None) == _lib.ERR_INVALID_VALUE      # mode
+    assert f(ODD, 5, 0.0, 1.0, 1, 0, 0, 0, None) == _lib.ERR_MISALIGNED
+    assert f(ODD, 5, 0.0, 1.0, 1, 0, 1, 0, None) == _lib.ERR_MISALIGNED          # bf16 needs 2 bytes
+    # ceil(9/4) = 3 blocks from 2^64 - 2 would pass 2^64
+    assert f(FAKE, 9, 0.0, 1.0, 1, 2 ** 64 - 2, 0, 0, None) == _lib.ERR_COUNTER_OVERFLOW
+    assert f(FAKE, 0, 0.0, 1.0, 1, 0, 0, 0, None) == _lib.OK                      # n = 0: no-op
+    assert f(None, 0, 0.0, 1.0, 1, 0, 0, 0, None) == _lib.OK
+
+
+def test_uniform_validation(lib):
+    f = lib.nrng_uniform
+    assert f(None, 3, 1, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(ctypes.c_void_p(0x100002), 3, 1, 0, None) == _lib.ERR_MISALIGNED
+    assert f(FAKE, 5, 1, 2 ** 64 - 1, None) == _lib.ERR_COUNTER_OVERFLOW
+    assert f(FAKE, 0, 1, 0, None) == _lib.OK
+
+
+def test_polar_workspace_and_validation(lib):
+    b = ctypes.c_size_t(0)
+    assert lib.nrng_polar_workspace_size(-1, ctypes.byref(b)) == _lib.ERR_INVALID_VALUE
+    assert lib.nrng_polar_workspace_size(1 << 28, ctypes.byref(b)) == _lib.OK
+    ws = b.value
+    # one 8-byte word per tile of 2048 candidates at the 0.78 budget + 64-byte header
+    tiles = ((1 << 27) + 12 * (int(np.sqrt(1 << 27)) + 1) + 16) * 100
+    tiles = (tiles + 2048 * 78 - 1) // (2048 * 78) + 1
+    assert ws == (64 + 8 * tiles + 255) // 256 * 256
+    blocks = ctypes.c_uint64(0)
+    assert lib.nrng_polar_max_blocks(1 << 28, ctypes.byref(blocks)) == _lib.OK
+    assert blocks.value == tiles * 1024
+    # workspace too small / missing
+    f = lib.nrng_polar
+    assert f(FAKE, 100, 0.0, 1.0, 1, 0, 0, 0, FAKE, 8, None, None, None) == _lib.ERR_WORKSPACE
+    assert f(FAKE, 100, 0.0, 1.0, 1, 0, 0, 0, None, 1 << 20, None, None, None) == _lib.ERR_WORKSPACE
+    assert f(FAKE, 100, 0.0, -2.0, 1, 0, 0, 0, FAKE, 1 << 20, None, None, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, 100, 0.0, 1.0, 1, 2 ** 64 - 5, 0, 0, FAKE, 1 << 20, None, None, None) == \
+        _lib.ERR_COUNTER_OVERFLOW
+    assert f(FAKE, 100, 0.0, 1.0, 1, 0, 0, 0, ctypes.c_void_p(0x100004), 1 << 20, None, None, None) == \
+        _lib.ERR_MISALIGNED
+    assert f(FAKE, (1 << 48) + 1, 0.0, 1.0, 1, 0, 0, 0, FAKE, 1 << 40, None, None, None) == \
+        _lib.ERR_INVALID_VALUE
+
+
+def _desc(ns, methods):
+    d = np.zeros(len(ns), dtype=STREAM_DESC)
+    d["n"] = ns
+    d["offset"] = np.concatenate([[0], np.cumsum(ns)[:-1]])
+    d["sigma"] = 1.0
+    d["method"] = methods
+    d["key"] = np.arange(len(ns))
+    return d
+
+
+def test_batched_workspace_size(lib):
+    d = _desc([100, 1000, 0, 5000], [0, 1, 1, 1])
+    b = ctypes.c_size_t(0)
+    assert lib.nrng_batched_workspace_size(d.ctypes.data_as(ctypes.c_void_p), len(d), ctypes.byref(b)) == _lib.OK
+    k = len(d)
+    fixed = (64 + (k + 1) * 8 + k * 8 + k * 4 + 255) // 256 * 256
+    # most slots over the configurations: the smallest Polar tile has 2*256*2 = 1024 candidates
+    worst = 0
+    for threads, bpt in [(256, 2), (256, 4), (256, 8), (128, 4), (128, 8), (512, 2)]:
+        cand = 2 * threads * bpt
+        s = 0
+        for n in (1000, 5000):
+            npairs = (n + 1) // 2
+            need = npairs + 12 * (int(np.sqrt(npairs)) + 1) + 16
+            s += (need * 100 + cand * 78 - 1) // (cand * 78) + 1
+        worst = max(worst, s)
+    assert b.value == fixed + 8 * worst
+    f = lib.nrng_batched
+    assert f(FAKE, FAKE, -1, 0, 0, FAKE, 1 << 20, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, FAKE, 4, 0, 0, None, 1 << 20, None) == _lib.ERR_WORKSPACE
+    assert f(FAKE, FAKE, 4, 0, 0, ctypes.c_void_p(0x100008), 1 << 20, None) == _lib.ERR_MISALIGNED
+    assert f(FAKE, FAKE, 4, 0, 0, FAKE, 16, None) == _lib.ERR_WORKSPACE
+    assert f(FAKE, FAKE, 0, 0, 0, FAKE, 16, None) == _lib.OK
+
+
+def test_reparam_validation(lib):
+    f = lib.nrng_reparam_fwd
+    assert f(FAKE, FAKE, FAKE, 12, 5, 1, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE     # 5 does not divide 12
+    assert f(FAKE, FAKE, FAKE, 12, 0, 1, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(None, FAKE, FAKE, 12, 12, 1, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(ODD, FAKE, FAKE, 12, 12, 1, 1, 0, 0, None) == _lib.ERR_MISALIGNED
+    g = lib.nrng_reparam_bwd
+    assert g(None, None, FAKE, 12, 12, 1, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE
+    assert g(None, FAKE, FAKE, 12, 12, 1, 1, 2 ** 64 - 1, 0, None) == _lib.ERR_COUNTER_OVERFLOW
+
+
+def test_config_table(lib):
+    n = lib.nrng_batched_config_count()
+    assert n == 6
+    t, b = ctypes.c_int32(0), ctypes.c_int32(0)
+    seen = set()
+    for c in range(n):
+        assert lib.nrng_batched_config_info(c, ctypes.byref(t), ctypes.byref(b)) == _lib.OK
+        seen.add((t.value, b.value))
+        assert t.value % 32 == 0 and 2 * t.value * b.value <= 4096
+    assert len(seen) == n
+    assert lib.nrng_batched_config_info(n, ctypes.byref(t), ctypes.byref(b)) == _lib.ERR_INVALID_VALUE
+    c = ctypes.c_int32(0)
+    assert lib.nrng_batched_set_config(0, 1, 4) == _lib.OK
+    assert lib.nrng_batched_get_config(0, 1, ctypes.byref(c)) == _lib.OK and c.value == 4
+    assert lib.nrng_batched_set_config(0, 1, -1) == _lib.OK
+    assert lib.nrng_batched_get_config(0, 1, ctypes.byref(c)) == _lib.OK and c.value == 1
+    assert lib.nrng_batched_set_config(0, 1, 99) == _lib.ERR_INVALID_VALUE

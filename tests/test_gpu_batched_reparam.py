@@ -1,0 +1,200 @@
+"""GPU parity of the batched launch (every configuration, graph replay,
+autotuner, device-side descriptor errors) and of the reparameterised sample
+and its autograd backward, against the FP64 oracle through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1004_3105_gb300 as nr
+from gpu_helpers import assert_close, sync
+from paper_1004_3105_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(k, len_lo, len_hi, methods, align, dtype=torch.float32, seed=W.BATCH_SEED):
+    wl = W.batched_workload(k=k, seed=seed, methods=methods, len_lo=len_lo, len_hi=len_hi, align=align)
+    desc = nr.stream_descriptors(wl.offset, wl.n, wl.mu, wl.sigma, wl.key, wl.counter, wl.method)
+    pad = 64
+    out = torch.full((wl.total + pad,), -12345.0, dtype=dtype, device="cuda")
+    ws = torch.empty(max(nr.nrng_batched_workspace_size(desc), 256), dtype=torch.uint8, device="cuda")
+    return wl, desc, nr.descriptors_to_device(desc), out, ws
+
+
+def check_batch(wl, out, mode, what):
+    ref = oracle.batched(wl.total, wl.as_dict())
+    got = out[:wl.total]
+    for j in range(len(wl.n)):
+        o, n = int(wl.offset[j]), int(wl.n[j])
+        assert_close(got[o:o + n], ref[o:o + n], float(wl.mu[j]), float(wl.sigma[j]), mode,
+                     f"{what} stream {j} (method {wl.method[j]}, n {n})")
+    sentinel = float(torch.tensor(-12345.0, dtype=out.dtype).float())
+    tail = out[wl.total:].float().cpu().numpy()
+    assert np.all(tail == sentinel)
+    # gaps between aligned streams stay untouched
+    mask = np.ones(wl.total, dtype=bool)
+    for j in range(len(wl.n)):
+        mask[int(wl.offset[j]):int(wl.offset[j]) + int(wl.n[j])] = False
+    if mask.any():
+        assert np.all(got.float().cpu().numpy()[mask] == sentinel)
+
+
+@pytest.mark.parametrize("config", range(6))
+def test_batched_every_config(config):
+    wl, desc, d_desc, out, ws = make_batch(64, 1, 20000, "mixed", align=1)
+    nr.nrng_batched_set_config(torch.float32, "accurate", config)
+    try:
+        nr.nrng_batched(out, d_desc, len(desc), ws, "accurate")
+        assert nr.nrng_get_status(ws) == 0
+    finally:
+        nr.nrng_batched_set_config(torch.float32, "accurate", -1)
+    check_batch(wl, out, "accurate", f"config {config}")
+
+
+@pytest.mark.parametrize("mode", ["accurate", "fast"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("methods,align", [("b1", 4), ("polar", 2), ("mixed", 1)])
+def test_batched_modes_dtypes(mode, dtype, methods, align):
+    wl, desc, d_desc, out, ws = make_batch(48, 1, 30000, methods, align, dtype)
+    nr.nrng_batched(out, d_desc, len(desc), ws, mode)
+    assert nr.nrng_get_status(ws) == 0
+    check_batch(wl, out, mode, f"{methods} {mode} {dtype}")
+
+
+def test_batched_full_workload_sampled():
+    """4096 streams, lengths log-uniform in [1e2, 1e6] (seed 7), mixed B1/P,
+    one persistent launch; a sample of 48 whole streams checked."""
+    wl, desc, d_desc, out, ws = make_batch(W.BATCH_STREAMS, W.BATCH_LEN_LO, W.BATCH_LEN_HI, "mixed", align=4)
+    nr.nrng_batched(out, d_desc, len(desc), ws, "accurate")
+    assert nr.nrng_get_status(ws) == 0
+    rng = np.random.Generator(np.random.PCG64(1))
+    pick = np.unique(np.concatenate([rng.choice(len(desc), 46, replace=False), [0, len(desc) - 1]]))
+    for j in pick:
+        o, n = int(wl.offset[j]), int(wl.n[j])
+        mu, sg, key = float(wl.mu[j]), float(wl.sigma[j]), int(wl.key[j])
+        ref = oracle.boxmuller(n, mu, sg, key, 0) if wl.method[j] == 0 else oracle.polar(n, mu, sg, key, 0)[0]
+        assert_close(out[o:o + n], ref, mu, sg, "accurate", f"stream {j}")
+
+
+def test_batched_graph_and_autotune_agree():
+    wl, desc, d_desc, out, ws = make_batch(96, 10, 50000, "mixed", align=1)
+    nr.nrng_batched(out, d_desc, len(desc), ws, "fast")
+    sync()
+    direct = out.clone()
+    out.fill_(0.0)
+    g = nr.BatchedGraph(out, d_desc, len(desc), ws, "fast")
+    g.launch()
+    g.launch()
+    sync()
+    assert torch.equal(out, direct)
+    g.close()
+    cfg, ms = nr.nrng_batched_autotune(out, d_desc, len(desc), ws, "fast", reps=2)
+    assert 0 <= cfg < nr.nrng_batched_config_count() and ms > 0
+    assert nr.nrng_batched_get_config(torch.float32, "fast") == cfg
+    out.fill_(0.0)
+    nr.nrng_batched(out, d_desc, len(desc), ws, "fast")
+    sync()
+    nr.nrng_batched_set_config(torch.float32, "fast", -1)
+    # the outputs do not depend on the tile shape
+    assert torch.equal(out, direct)
+
+
+def test_batched_device_descriptor_errors():
+    wl, desc, d_desc, out, ws = make_batch(8, 10, 1000, "mixed", align=1)
+    bad = desc.copy()
+    bad["sigma"][3] = -1.0
+    d_bad = nr.descriptors_to_device(bad)
+    before = out.clone()
+    nr.nrng_batched(out, d_bad, len(bad), ws, "accurate")
+    assert nr.nrng_get_status(ws) == nr._lib.ERR_INVALID_VALUE
+    assert torch.equal(out, before)          # nothing written
+    # a workspace large enough for the tables but not for the tile words
+    small = torch.empty(512, dtype=torch.uint8, device="cuda")
+    nr.nrng_batched(out, d_desc, len(desc), small, "accurate")
+    assert nr.nrng_get_status(small) == nr._lib.ERR_WORKSPACE
+    assert torch.equal(out, before)
+    # and the context is fine afterwards
+    nr.nrng_batched(out, d_desc, len(desc), ws, "accurate")
+    assert nr.nrng_get_status(ws) == 0
+    check_batch(wl, out, "accurate", "after errors")
+
+
+# ------------------------------------------------------------------ reparam
+@pytest.mark.parametrize("mode", ["accurate", "fast"])
+def test_reparam_config_c5(mode):
+    wl = W.reparam_workload()
+    shape = W.REPARAM_SHAPE
+    n = int(np.prod(shape))
+    mu = torch.from_numpy(wl.mu).cuda()
+    sigma = torch.from_numpy(wl.sigma).cuda()
+    x = torch.empty(shape, dtype=torch.float32, device="cuda")
+    nr.nrng_reparam_fwd(x, mu, sigma, W.KEY_REPARAM, 0, mode)
+    sync()
+    xr = oracle.reparam_fwd(wl.mu, wl.sigma, n, 1, W.KEY_REPARAM, 0)
+    z = oracle.boxmuller(n, 0.0, 1.0, W.KEY_REPARAM, 0)
+    got = x.cpu().numpy().ravel().astype(np.float64)
+    # x = mu + sigma z: bound in z units scaled by each element's sigma
+    s64 = wl.sigma.ravel().astype(np.float64)
+    from gpu_helpers import TOL, ulp_fmt
+    bnd = TOL[mode] * s64 * np.maximum(1, np.abs(z)) + ulp_fmt(xr, torch.float32)
+    assert np.all(np.abs(got - xr) <= bnd)
+    # backward of loss = sum(w x^2): g = 2 w x
+    g = (2.0 * torch.from_numpy(wl.w).cuda() * x).contiguous()
+    dmu = torch.empty_like(mu)
+    dsig = torch.empty_like(sigma)
+    nr.nrng_reparam_bwd(dmu, dsig, g, W.KEY_REPARAM, 0, mode)
+    sync()
+    gh = g.cpu().numpy().ravel()
+    rdmu, rdsig = oracle.reparam_bwd(gh, n, 1, W.KEY_REPARAM, 0)
+    assert np.array_equal(dmu.cpu().numpy().ravel(), gh)
+    gz = np.abs(gh.astype(np.float64))
+    assert np.all(np.abs(dsig.cpu().numpy().ravel() - rdsig) <= TOL[mode] * gz * np.maximum(1, np.abs(z)) +
+                  ulp_fmt(rdsig, torch.float32))
+
+
+@pytest.mark.parametrize("pshape", [(1,), (8192,), (1024, 1), (1024, 8192)])
+def test_reparam_autograd_broadcast(pshape):
+    shape = (1024, 8192) if pshape != (1,) else (256, 1024)
+    n = int(np.prod(shape))
+    rng = np.random.Generator(np.random.PCG64(2))
+    mu_h = rng.standard_normal(size=pshape).astype(np.float32)
+    sg_h = rng.uniform(0.1, 2.0, size=pshape).astype(np.float32)
+    w_h = rng.uniform(-1, 1, size=shape).astype(np.float32)
+    mu = torch.from_numpy(mu_h).cuda().requires_grad_(True)
+    sg = torch.from_numpy(sg_h).cuda().requires_grad_(True)
+    w = torch.from_numpy(w_h).cuda()
+    x = nr.Reparam.apply(mu, sg, shape, W.KEY_REPARAM, 0, "accurate")
+    loss = (w * x * x).sum()
+    loss.backward()
+    m, inner = nr.broadcast_layout(pshape, shape)
+    g = (2.0 * w * x).detach().cpu().numpy().ravel()
+    rdmu, rdsig = oracle.reparam_bwd(g, m, inner, W.KEY_REPARAM, 0)
+    # sums of n/m float terms: float32 accumulation in any order stays within
+    # (count * 2^-24 + 4e-6) of the sum of absolute terms
+    z = oracle.boxmuller(n, 0.0, 1.0, W.KEY_REPARAM, 0)
+    absg = np.abs(g.astype(np.float64))
+    idx = (np.arange(n) // inner) % m
+    abs_gz = np.bincount(idx, weights=absg * np.maximum(1, np.abs(z)), minlength=m)
+    abs_g = np.bincount(idx, weights=absg, minlength=m)
+    cnt = n // m
+    slack = cnt * 2.0 ** -24 + 4e-6
+    assert np.all(np.abs(mu.grad.cpu().numpy().ravel() - rdmu) <= slack * abs_g + 1e-6)
+    assert np.all(np.abs(sg.grad.cpu().numpy().ravel() - rdsig) <= slack * abs_gz + 1e-6)
+
+
+def test_reparam_recompute_equals_stream():
+    """z seen by forward (mu 0, sigma 1) and by backward (g 1 -> dsigma = z) is
+    bitwise the nrng_boxmuller stream of the same key and counter."""
+    n = (1 << 20) + 6
+    for mode in ("accurate", "fast"):
+        zero = torch.zeros(n, device="cuda")
+        one = torch.ones(n, device="cuda")
+        x = torch.empty(n, device="cuda")
+        nr.nrng_reparam_fwd(x, zero, one, 42, 9, mode)
+        dsig = torch.empty(n, device="cuda")
+        nr.nrng_reparam_bwd(None, dsig, one, 42, 9, mode)
+        ref = torch.empty(n, device="cuda")
+        nr.nrng_boxmuller(ref, 0.0, 1.0, 42, 9, mode)
+        sync()
+        assert torch.equal(x, ref) and torch.equal(dsig, ref)

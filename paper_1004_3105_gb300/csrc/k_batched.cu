@@ -163,6 +163,7 @@ k_batched(BatchedParams bp)
     __shared__ PolarSmem<THREADS, BPT> sm;
     __shared__ long long s_item;
     __shared__ int s_stream;
+    __shared__ int s_skip;
     __shared__ nrng_stream_desc_t s_desc;
 
     const unsigned long long total_items = bp.hdr->aux[0];
@@ -188,6 +189,10 @@ k_batched(BatchedParams bp)
             }
             s_item = item;
             s_stream = j;
+            // One thread reads the stream's completion flag for the whole CTA:
+            // every thread must take the same branch around polar_tile's
+            // barriers and full-warp ballots.
+            s_skip = (j >= 0 && s_desc.method == NRNG_POLAR) ? ld_relaxed_s32(bp.stream_done + j) : 0;
         }
         __syncthreads();
         const long long item = s_item;
@@ -217,7 +222,7 @@ k_batched(BatchedParams bp)
             ps.next_counter = nullptr;
             ps.pair_cand = nullptr;
             ps.silent_tile = -1;
-            if (ld_relaxed_s32(ps.done) != 0) {
+            if (s_skip != 0) {
                 // Stream complete: every later tile's prefix is >= npairs.
                 if (threadIdx.x == 0)
                     st_relaxed(ps.status + t, kFlagPrefix | (unsigned long long)ps.npairs);

@@ -136,6 +136,31 @@ int32_t nrng_polar(void *d_out, int64_t n, float mu, float sigma, uint64_t key,
                    size_t ws_bytes, uint64_t *d_next_counter, int64_t *d_pair_candidate,
                    nrng_stream_t stream);
 
+/* Polar without a workspace, for callers that cannot allocate device memory
+ * (no counterpart in the paper).  Some callers cannot obtain the workspace
+ * nrng_polar needs: code running inside a host application that owns the
+ * device memory budget and forbids allocations of its own, or a
+ * latency-critical loop that avoids cudaMalloc because it can synchronise the
+ * device.  This call computes exactly what nrng_polar computes (same kernel,
+ * same outputs) but keeps its scratch in a fixed 1 MiB device array inside the
+ * library, so it allocates nothing; the caller passes only outputs.
+ *   n: at most 2^28 (268435456); a larger n returns NRNG_ERR_WORKSPACE and
+ *     enqueues nothing.
+ *   d_next_counter, d_pair_candidate: as nrng_polar (nullable).
+ *   d_status (nullable): one int32 that receives the call's device status
+ *     word (NRNG_OK, NRNG_ERR_TIMEOUT, NRNG_ERR_EXHAUSTED) once the kernel is
+ *     done, in stream order.
+ * The array is held by every GPU that loads the library until the process
+ * exits and is shared by every call on that device: each call clears what it
+ * uses first, so calls ordered on the GPU are independent, but calls that
+ * overlap on the GPU (unordered streams) race on it.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. */
+int32_t nrng_polar_noalloc(void *d_out, int64_t n, float mu, float sigma, uint64_t key,
+                           uint64_t counter, int32_t dtype, int32_t mode,
+                           uint64_t *d_next_counter, int64_t *d_pair_candidate,
+                           int32_t *d_status, nrng_stream_t stream);
+
 /* Workspace bytes nrng_batched needs for the k streams described in h_desc
  * (host copy of the descriptors).  Pure host computation. */
 int32_t nrng_batched_workspace_size(const nrng_stream_desc_t *h_desc, int32_t k,

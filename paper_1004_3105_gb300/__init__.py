@@ -7,6 +7,6 @@ from .nrng import (  # noqa: F401
     ACCURATE, B1, FAST, POLAR, STREAM_DESC, BatchedGraph, Reparam, broadcast_layout, descriptors_to_device,
     nrng_batched, nrng_batched_autotune, nrng_batched_config_count, nrng_batched_config_info,
     nrng_batched_get_config, nrng_batched_set_config, nrng_batched_workspace_size, nrng_boxmuller,
-    nrng_get_status, nrng_polar, nrng_polar_max_blocks, nrng_polar_workspace_size, nrng_reparam_bwd,
+    nrng_get_status, nrng_polar, nrng_polar_max_blocks, nrng_polar_noalloc, nrng_polar_workspace_size, nrng_reparam_bwd,
     nrng_reparam_fwd, nrng_uniform, polar_workspace, raise_on_status, stream_descriptors,
 )

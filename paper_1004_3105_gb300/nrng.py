@@ -119,6 +119,18 @@ def nrng_polar(out: torch.Tensor, mu: float, sigma: float, key: int, counter: in
           "nrng_polar")
 
 
+def nrng_polar_noalloc(out: torch.Tensor, mu: float, sigma: float, key: int, counter: int, mode="accurate",
+                       next_counter: torch.Tensor = None, pair_candidate: torch.Tensor = None,
+                       status: torch.Tensor = None, stream=None) -> None:
+    """nrng_polar with the library's fixed device scratch instead of a caller
+    workspace, for callers that cannot allocate device memory (n <= 2^28).
+    status: optional int32 CUDA tensor that receives the device status word."""
+    check(load().nrng_polar_noalloc(_dev(out, "out"), out.numel(), float(mu), float(sigma), _u64(key), _u64(counter),
+                                    _dtype(out), _mode(mode), _dev(next_counter, "next_counter"),
+                                    _dev(pair_candidate, "pair_candidate"), _dev(status, "status"), _stream(stream)),
+          "nrng_polar_noalloc")
+
+
 def nrng_get_status(workspace: torch.Tensor, stream=None) -> int:
     """The status word a workspace call left (synchronises the stream)."""
     v = ctypes.c_int32(0)

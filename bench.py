@@ -299,6 +299,39 @@ class Step:
                 raise RuntimeError(f"device status {nr._lib.STATUS.get(st, st)}")
 
 
+def precision_sweep(step, K, W, peak):
+    """{B1, Polar} x {accurate, fast} x {f32, bf16, f16} at N = 2^28."""
+    import torch
+    nr = step.nr
+    out = {}
+    bufs = {torch.float32: step.out_b1, torch.bfloat16: step.out_b1.view(torch.bfloat16)[:N_FULL],
+            torch.float16: step.out_b1.view(torch.float16)[:N_FULL]}
+    names = {torch.float32: "f32", torch.bfloat16: "bf16", torch.float16: "f16"}
+    for method in ("b1", "polar"):
+        for mode in ("accurate", "fast"):
+            for dt, buf in bufs.items():
+                def run():
+                    if method == "b1":
+                        nr.nrng_boxmuller(buf, 1.5, 0.25, KEY, step.base, mode)
+                    else:
+                        nr.nrng_polar(buf, 1.5, 0.25, KEY, step.base, step.ws_p, mode)
+                for _ in range(W):
+                    run()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(K):
+                    run()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / K
+                by = N_FULL * buf.element_size()
+                gbs = by / (ms * 1e-3) / 1e9
+                out[f"{method}_{mode}_{names[dt]}"] = {"ms": round(ms, 4), "normals_per_s": N_FULL / (ms * 1e-3),
+                                                       "GB_per_s": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4)}
+    step.check_status()
+    return out
+
+
 def cpu_oracle_sample(seconds_budget: float = 12.0):
     """Times the FP64 oracle (single thread) on a bounded sample of the step's
     mix: B1 and Polar at equal counts plus a slice of the batched streams and
@@ -452,6 +485,13 @@ def bench_ours(args):
                 "traffic": recorded_traffic(kernel_names[dom]),
                 "algorithmic_bytes_per_launch": alg_bytes[dom]}
 
+    # ---- precision sweep at N = 2^28 (mu 1.5, sigma 0.25): each variant timed
+    # alone with CUDA events (mean of K launches after W warm-ups), not part of
+    # the step
+    sweep = {}
+    if not args.no_sweep:
+        sweep = precision_sweep(step, K, args.warmup, peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(args.cpu_seconds)
@@ -466,7 +506,7 @@ def bench_ours(args):
                        "N": N_FULL, "batched_normals": step.batch_total, "reparam_shape": list(step.rep_shape),
                        "l2": "every output > L2 (1 GiB per single-stream kernel); no flush",
                        "parallelism": f"replicas x{world}"},
-            "parts": parts, "roofline": roofline, "clocks": clocks.summary(),
+            "parts": parts, "sweep": sweep, "roofline": roofline, "clocks": clocks.summary(),
             "e2e": e2e, "gpu_launches": K * step.our_launches_per_step, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -485,6 +525,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -39,19 +39,25 @@ k_b1(T *__restrict__ out, int64_t n, int64_t nblocks, float mu, float sigma, uin
      const RoundKeys rk)
 {
     const int64_t stride = (int64_t)gridDim.x * kB1Threads;
-    for (int64_t b = (int64_t)blockIdx.x * kB1Threads + threadIdx.x; b < nblocks; b += stride) {
-        const uint4 w = philox_block(counter + (uint64_t)b, rk);
-        float x0, y0, x1, y1;
-        b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
-        b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
-        const int64_t i = 4 * b;
-        if (ALIGNED && i + 4 <= n) {
-            store4_aligned(out + i, x0, y0, x1, y1);
-        } else {
-            if (i < n) store1(out + i, x0);
-            if (i + 1 < n) store1(out + i + 1, y0);
-            if (i + 2 < n) store1(out + i + 2, x1);
-            if (i + 3 < n) store1(out + i + 3, y1);
+    // two independent blocks per iteration give the scheduler more to overlap
+    for (int64_t b = (int64_t)blockIdx.x * kB1Threads + threadIdx.x; b < nblocks; b += 2 * stride) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int64_t bq = b + q * stride;
+            if (bq >= nblocks) break;
+            const uint4 w = philox_block(counter + (uint64_t)bq, rk);
+            float x0, y0, x1, y1;
+            b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
+            b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
+            const int64_t i = 4 * bq;
+            if (ALIGNED && i + 4 <= n) {
+                store4_aligned(out + i, x0, y0, x1, y1);
+            } else {
+                if (i < n) store1(out + i, x0);
+                if (i + 1 < n) store1(out + i + 1, y0);
+                if (i + 2 < n) store1(out + i + 2, x1);
+                if (i + 3 < n) store1(out + i + 3, y1);
+            }
         }
     }
 }

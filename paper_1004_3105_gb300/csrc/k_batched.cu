@@ -22,10 +22,11 @@
 namespace nrng {
 
 // ------------------------------------------------------------ configs -----
-// (threads per CTA, Philox blocks per thread per tile); the Polar staging
-// buffer of the largest is 2 * 256 * 8 candidates * 10 bytes = 40 KB.
+// (threads per CTA, Philox blocks per thread per tile).  A Polar tile of
+// 2 * threads * blocks candidates stages 20 bytes per candidate in shared
+// memory, so 2048 candidates (40 KB) is the largest static tile.
 static const BatchedConfig kConfigs[] = {
-    {256, 2}, {256, 4}, {256, 8}, {128, 4}, {128, 8}, {512, 2},
+    {256, 2}, {256, 4}, {128, 4}, {128, 2}, {512, 2}, {512, 1},
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
@@ -156,8 +157,17 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
 }
 
 // ------------------------------------------------------------ main --------
+// The batched kernel carries both tile bodies (B1 and Polar), so it is
+// compiled for fewer resident threads than the single-stream Polar kernel
+// (768 per SM, about 85 registers a thread).
+template <int THREADS, int MODE>
+struct BatchedOccupancy {
+    static constexpr int kThreads = 768;
+    static constexpr int kMinBlocks = (kThreads / THREADS) > 0 ? (kThreads / THREADS) : 1;
+};
+
 template <int THREADS, int BPT, int MODE, typename T>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, (BatchedOccupancy<THREADS, MODE>::kMinBlocks))
 k_batched(BatchedParams bp)
 {
     __shared__ PolarSmem<THREADS, BPT> sm;
@@ -200,8 +210,7 @@ k_batched(BatchedParams bp)
         const int j = s_stream;
         const nrng_stream_desc_t d = s_desc;
         const int64_t t = item - bp.item_prefix[j];
-        RoundKeys rk;
-        make_round_keys(d.key, rk);
+        const StreamKey rk{(uint32_t)d.key, (uint32_t)(d.key >> 32)};
         T *out = reinterpret_cast<T *>(out_base) + d.offset;
         bool ok = true;
         if (d.method == NRNG_B1) {
@@ -257,10 +266,10 @@ static cudaError_t batched_config_dispatch(const BatchedParams &bp, int config, 
     switch (config) {
     case 0: return batched_main<256, 2, MODE, T>(bp, s);
     case 1: return batched_main<256, 4, MODE, T>(bp, s);
-    case 2: return batched_main<256, 8, MODE, T>(bp, s);
-    case 3: return batched_main<128, 4, MODE, T>(bp, s);
-    case 4: return batched_main<128, 8, MODE, T>(bp, s);
-    default: return batched_main<512, 2, MODE, T>(bp, s);
+    case 2: return batched_main<128, 4, MODE, T>(bp, s);
+    case 3: return batched_main<128, 2, MODE, T>(bp, s);
+    case 4: return batched_main<512, 2, MODE, T>(bp, s);
+    default: return batched_main<512, 1, MODE, T>(bp, s);
     }
 }
 

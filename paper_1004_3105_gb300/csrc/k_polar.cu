@@ -4,19 +4,15 @@
 // The paper vectorises P by generating vectors of (x, y, s), compressing out
 // the rejected triples and buffering the variable-length result (Sec. 2's
 // vector gather; Sec. 4, RANN3B/RANN3).  Here the compress is a decoupled
-// look-back scan over tiles of 2048 candidates:
-//   1. a persistent CTA takes the next tile id from a global counter (dynamic
-//      ids, so a tile only ever waits on tiles already owned by running CTAs);
-//   2. each thread draws kPolarRows Philox blocks (two candidates each), tests
-//      0 < kx'^2 + ky'^2 < 2^46 exactly in 64-bit integers, and ranks its
-//      accepted candidates inside the warp with ballot/popc;
-//   3. one warp scans the 32 (row, warp) counts, publishes the tile aggregate,
-//      looks back for the exclusive prefix and publishes the inclusive one;
-//   4. accepted lattice points are staged in shared memory in candidate order,
-//      then every thread transforms a dense run of them (no idle lanes from
-//      rejections) and stores pairs at their global positions, coalesced.
-// The tile holding the ceil(n/2)-th accepted pair writes next_counter and
-// raises `done`, after which CTAs stop taking tiles.
+// look-back scan over tiles of kPolarCandPerTile candidates (polar_tile in
+// tiles.cuh): a persistent CTA takes the next tile id from a global counter
+// (dynamic ids, so a tile only ever waits on tiles already owned by running
+// CTAs); each warp draws its candidates, tests 0 < kx'^2 + ky'^2 < 2^46
+// exactly in 64-bit integers, compacts the accepted ones into its own
+// shared-memory segment by ballot/popc rank, runs step 4 densely over it and,
+// once warp 0 has looked back for the tile's prefix, copies its runs to their
+// global positions.  The tile holding the ceil(n/2)-th accepted pair writes
+// next_counter and raises `done`, after which CTAs stop taking tiles.
 #include <algorithm>
 
 #include "tiles.cuh"
@@ -24,7 +20,7 @@
 namespace nrng {
 
 template <int MODE, typename T, bool ALIGNED>
-__global__ void __launch_bounds__(kPolarThreads)
+__global__ void __launch_bounds__(kPolarThreads, (PolarOccupancy<kPolarThreads, MODE>::kMinBlocks))
 k_polar(const PolarParams p)
 {
     __shared__ PolarSmem<kPolarThreads, kPolarRows> sm;

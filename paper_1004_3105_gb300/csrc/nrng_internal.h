@@ -38,9 +38,9 @@ static_assert(sizeof(WsHeader) == 64, "workspace header is 64 bytes");
 
 // ---------------------------------------------------------------- Polar --
 constexpr int kPolarThreads = 256;
-constexpr int kPolarRows = 4;                                  // Philox blocks per thread per tile
-constexpr int kPolarBlocksPerTile = kPolarThreads * kPolarRows; // 1024
-constexpr int kPolarCandPerTile = 2 * kPolarBlocksPerTile;      // 2048
+constexpr int kPolarRows = 8;                                  // Philox blocks per thread per tile
+constexpr int kPolarBlocksPerTile = kPolarThreads * kPolarRows; // 2048
+constexpr int kPolarCandPerTile = 2 * kPolarBlocksPerTile;      // 4096
 
 struct PolarParams {
     void *out;

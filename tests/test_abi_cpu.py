@@ -75,13 +75,13 @@ def test_polar_workspace_and_validation(lib):
     assert lib.nrng_polar_workspace_size(-1, ctypes.byref(b)) == _lib.ERR_INVALID_VALUE
     assert lib.nrng_polar_workspace_size(1 << 28, ctypes.byref(b)) == _lib.OK
     ws = b.value
-    # one 8-byte word per tile of 2048 candidates at the 0.78 budget + 64-byte header
+    # one 8-byte word per tile of 4096 candidates at the 0.78 budget + 64-byte header
     tiles = ((1 << 27) + 12 * (int(np.sqrt(1 << 27)) + 1) + 16) * 100
-    tiles = (tiles + 2048 * 78 - 1) // (2048 * 78) + 1
+    tiles = (tiles + 4096 * 78 - 1) // (4096 * 78) + 1
     assert ws == (64 + 8 * tiles + 255) // 256 * 256
     blocks = ctypes.c_uint64(0)
     assert lib.nrng_polar_max_blocks(1 << 28, ctypes.byref(blocks)) == _lib.OK
-    assert blocks.value == tiles * 1024
+    assert blocks.value == tiles * 2048
     # workspace too small / missing
     f = lib.nrng_polar
     assert f(FAKE, 100, 0.0, 1.0, 1, 0, 0, 0, FAKE, 8, None, None, None) == _lib.ERR_WORKSPACE
@@ -113,7 +113,7 @@ def test_batched_workspace_size(lib):
     fixed = (64 + (k + 1) * 8 + k * 8 + k * 4 + 255) // 256 * 256
     # most slots over the configurations: the smallest Polar tile has 2*256*2 = 1024 candidates
     worst = 0
-    for threads, bpt in [(256, 2), (256, 4), (256, 8), (128, 4), (128, 8), (512, 2)]:
+    for threads, bpt in [(256, 2), (256, 4), (128, 4), (128, 2), (512, 2), (512, 1)]:
         cand = 2 * threads * bpt
         s = 0
         for n in (1000, 5000):

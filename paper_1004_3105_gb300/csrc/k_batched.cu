@@ -22,11 +22,11 @@
 namespace nrng {
 
 // ------------------------------------------------------------ configs -----
-// (threads per CTA, Philox blocks per thread per tile).  A Polar tile of
-// 2 * threads * blocks candidates stages 20 bytes per candidate in shared
-// memory, so 2048 candidates (40 KB) is the largest static tile.
+// (threads per CTA, Philox blocks per thread per tile).  A Polar tile stages
+// at most 64 accepted points per warp and row, 10 bytes each, in shared
+// memory: 40 KB for 256 x 8.
 static const BatchedConfig kConfigs[] = {
-    {256, 2}, {256, 4}, {128, 4}, {128, 2}, {512, 2}, {512, 1},
+    {256, 4}, {256, 8}, {128, 8}, {512, 4}, {128, 4}, {512, 2},
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
@@ -40,7 +40,8 @@ __host__ __device__ inline int64_t b1_items(int64_t n, int64_t tile_blocks)
     return (nblocks + tile_blocks - 1) / tile_blocks;
 }
 
-// Items and status slots of one stream; -1 items marks an invalid descriptor.
+// Items and status slots of one stream; -1 items marks an invalid descriptor,
+// -2 a counter that would pass 2^64.
 __host__ __device__ inline void stream_items(const nrng_stream_desc_t &d, int threads, int bpt,
                                              int64_t &items, int64_t &slots)
 {
@@ -84,6 +85,8 @@ size_t batched_workspace_bytes(const nrng_stream_desc_t *h_desc, int32_t k)
 }
 
 // ------------------------------------------------------------ prep --------
+// One CTA: every thread takes a contiguous run of descriptors, sums their
+// items and status slots, and one block-wide exclusive scan places them.
 constexpr int kPrepThreads = 1024;
 
 __global__ void __launch_bounds__(kPrepThreads)
@@ -94,64 +97,65 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_bad = 0;
     __syncthreads();
-    long long carry_i = 0, carry_s = 0;
-    for (int32_t c0 = 0; c0 < bp.k; c0 += kPrepThreads) {
-        const int32_t j = c0 + tid;
-        int64_t items = 0, slots = 0;
-        if (j < bp.k) {
-            stream_items(bp.desc[j], threads, bpt, items, slots);
-            if (items < 0) {
-                atomicMax(&s_bad, items == -2 ? kStatusOverflow : kStatusInvalid);
-                items = 0;
-                slots = 0;
-            }
+    const int32_t per = (bp.k + kPrepThreads - 1) / kPrepThreads;
+    const int32_t j0 = tid * per;
+    const int32_t j1 = (j0 + per < bp.k) ? j0 + per : bp.k;
+    long long mi = 0, ms = 0;
+    for (int32_t j = j0; j < j1; ++j) {
+        int64_t items, slots;
+        stream_items(bp.desc[j], threads, bpt, items, slots);
+        if (items < 0) {
+            atomicMax(&s_bad, items == -2 ? kStatusOverflow : kStatusInvalid);
+            items = 0;
+            slots = 0;
         }
-        // block-wide exclusive scan of (items, slots)
-        long long ii = items, is = slots;
+        mi += items;
+        ms += slots;
+    }
+    long long ii = mi, is = ms;   // inclusive within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long a = __shfl_up_sync(0xFFFFFFFFu, ii, o);
+        const long long b = __shfl_up_sync(0xFFFFFFFFu, is, o);
+        if (lane >= o) { ii += a; is += b; }
+    }
+    if (lane == 31) { s_wi[warp] = ii; s_ws[warp] = is; }
+    __syncthreads();
+    if (warp == 0) {
+        long long wi = s_wi[lane], ws = s_ws[lane];
+        const long long wi0 = wi, ws0 = ws;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const long long a = __shfl_up_sync(0xFFFFFFFFu, ii, o);
-            const long long b = __shfl_up_sync(0xFFFFFFFFu, is, o);
-            if (lane >= o) { ii += a; is += b; }
+            const long long a = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            const long long b = __shfl_up_sync(0xFFFFFFFFu, ws, o);
+            if (lane >= o) { wi += a; ws += b; }
         }
-        if (lane == 31) { s_wi[warp] = ii; s_ws[warp] = is; }
-        __syncthreads();
-        if (warp == 0) {
-            long long wi = s_wi[lane], ws = s_ws[lane];
-            const long long wi0 = wi, ws0 = ws;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long a = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-                const long long b = __shfl_up_sync(0xFFFFFFFFu, ws, o);
-                if (lane >= o) { wi += a; ws += b; }
-            }
-            s_wi[lane] = wi - wi0;
-            s_ws[lane] = ws - ws0;
-        }
-        __syncthreads();
-        if (j < bp.k) {
-            bp.item_prefix[j] = carry_i + s_wi[warp] + ii - items;
-            bp.slot_base[j] = carry_s + s_ws[warp] + is - slots;
-        }
-        // chunk totals: the last thread's inclusive values
-        __shared__ long long s_ti, s_ts;
-        if (tid == kPrepThreads - 1) { s_ti = s_wi[warp] + ii; s_ts = s_ws[warp] + is; }
-        __syncthreads();
-        carry_i += s_ti;
-        carry_s += s_ts;
-        __syncthreads();
+        s_wi[lane] = wi - wi0;   // exclusive warp offsets
+        s_ws[lane] = ws - ws0;
     }
-    if (tid == 0) {
-        bp.item_prefix[bp.k] = carry_i;
-        const size_t need = batched_layout(bp.k).tile_status + (size_t)carry_s * 8;
+    __syncthreads();
+    long long ci = s_wi[warp] + ii - mi, cs = s_ws[warp] + is - ms;   // exclusive for this thread
+    for (int32_t j = j0; j < j1; ++j) {
+        int64_t items, slots;
+        stream_items(bp.desc[j], threads, bpt, items, slots);
+        if (items < 0) { items = 0; slots = 0; }
+        bp.item_prefix[j] = ci;
+        bp.slot_base[j] = cs;
+        ci += items;
+        cs += slots;
+    }
+    if (tid == kPrepThreads - 1) {
+        bp.item_prefix[bp.k] = ci;
+        const size_t need = batched_layout(bp.k).tile_status + (size_t)cs * 8;
         int bad = s_bad;
         if (!bad && need > bp.ws_bytes) bad = kStatusWorkspace;
+        if (!bad && ci >= (1ll << 31)) bad = kStatusInvalid;   // item ids are 32-bit
         if (bad) {
             bp.hdr->status = bad;
             bp.hdr->done = 1;
             bp.hdr->aux[0] = 0;
         } else {
-            bp.hdr->aux[0] = (unsigned long long)carry_i;
+            bp.hdr->aux[0] = (unsigned long long)ci;
         }
     }
 }
@@ -166,6 +170,10 @@ struct BatchedOccupancy {
     static constexpr int kMinBlocks = (kThreads / THREADS) > 0 ? (kThreads / THREADS) : 1;
 };
 
+// Streams whose item prefix is cached in shared memory (as int32) for the
+// item -> stream search; more streams fall back to searching global memory.
+constexpr int kSmemStreams = 8192;
+
 template <int THREADS, int BPT, int MODE, typename T>
 __global__ void __launch_bounds__(THREADS, (BatchedOccupancy<THREADS, MODE>::kMinBlocks))
 k_batched(BatchedParams bp)
@@ -175,9 +183,16 @@ k_batched(BatchedParams bp)
     __shared__ int s_stream;
     __shared__ int s_skip;
     __shared__ nrng_stream_desc_t s_desc;
+    extern __shared__ int s_prefix[];   // item_prefix[0..k] when k <= kSmemStreams
 
     const unsigned long long total_items = bp.hdr->aux[0];
+    const bool cached = bp.k <= kSmemStreams;
+    if (cached) {
+        for (int j = threadIdx.x; j <= bp.k; j += THREADS) s_prefix[j] = (int)bp.item_prefix[j];
+        __syncthreads();
+    }
     char *out_base = static_cast<char *>(bp.out);
+    int last = 0;   // thread 0: stream of the previous item (items only increase)
     for (;;) {
         if (threadIdx.x == 0) {
             long long item = -1;
@@ -187,14 +202,26 @@ k_batched(BatchedParams bp)
             }
             int j = -1;
             if (item >= 0) {
-                // largest j with item_prefix[j] <= item (streams with no items
-                // share their prefix with the next stream; take the last)
-                int lo = 0, hi = bp.k;   // item_prefix[lo] <= item < item_prefix[hi]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) / 2;
-                    if (bp.item_prefix[mid] <= item) lo = mid; else hi = mid;
+                // largest j with item_prefix[j] <= item: gallop up from the
+                // previous stream, then bisect (empty streams share a prefix
+                // with the next one; the largest j is the non-empty one)
+                const int it32 = (int)item;
+                int lo = last, step = 1, hi;
+                for (;;) {
+                    hi = lo + step;
+                    if (hi >= bp.k) { hi = bp.k; break; }
+                    const int v = cached ? s_prefix[hi] : (int)bp.item_prefix[hi];
+                    if (v > it32) break;
+                    lo = hi;
+                    step <<= 1;
+                }
+                while (hi - lo > 1) {   // prefix[lo] <= item < prefix[hi]
+                    const int mid = (lo + hi) >> 1;
+                    const int v = cached ? s_prefix[mid] : (int)bp.item_prefix[mid];
+                    if (v <= it32) lo = mid; else hi = mid;
                 }
                 j = lo;
+                last = lo;
                 s_desc = bp.desc[j];
             }
             s_item = item;
@@ -209,7 +236,7 @@ k_batched(BatchedParams bp)
         if (item < 0) break;
         const int j = s_stream;
         const nrng_stream_desc_t d = s_desc;
-        const int64_t t = item - bp.item_prefix[j];
+        const int64_t t = item - (cached ? (long long)s_prefix[j] : bp.item_prefix[j]);
         const StreamKey rk{(uint32_t)d.key, (uint32_t)(d.key >> 32)};
         T *out = reinterpret_cast<T *>(out_base) + d.offset;
         bool ok = true;
@@ -250,13 +277,19 @@ template <int THREADS, int BPT, int MODE, typename T>
 static cudaError_t batched_main(const BatchedParams &bp, cudaStream_t s)
 {
     static int occ = 0;
+    const size_t dyn = (bp.k <= kSmemStreams) ? (size_t)(bp.k + 1) * sizeof(int) : 0;
     if (occ == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_batched<THREADS, BPT, MODE, T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((kSmemStreams + 1) * sizeof(int)));
+        if (e != cudaSuccess) return e;
         int o = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batched<THREADS, BPT, MODE, T>, THREADS, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batched<THREADS, BPT, MODE, T>, THREADS,
+                                                          (kSmemStreams + 1) * sizeof(int));
         if (e != cudaSuccess) return e;
         occ = std::max(o, 1);
     }
-    k_batched<THREADS, BPT, MODE, T><<<sm_count() * occ, THREADS, 0, s>>>(bp);
+    k_batched<THREADS, BPT, MODE, T><<<sm_count() * occ, THREADS, dyn, s>>>(bp);
     return cudaGetLastError();
 }
 
@@ -264,12 +297,12 @@ template <int MODE, typename T>
 static cudaError_t batched_config_dispatch(const BatchedParams &bp, int config, cudaStream_t s)
 {
     switch (config) {
-    case 0: return batched_main<256, 2, MODE, T>(bp, s);
-    case 1: return batched_main<256, 4, MODE, T>(bp, s);
-    case 2: return batched_main<128, 4, MODE, T>(bp, s);
-    case 3: return batched_main<128, 2, MODE, T>(bp, s);
-    case 4: return batched_main<512, 2, MODE, T>(bp, s);
-    default: return batched_main<512, 1, MODE, T>(bp, s);
+    case 0: return batched_main<256, 4, MODE, T>(bp, s);
+    case 1: return batched_main<256, 8, MODE, T>(bp, s);
+    case 2: return batched_main<128, 8, MODE, T>(bp, s);
+    case 3: return batched_main<512, 4, MODE, T>(bp, s);
+    case 4: return batched_main<128, 4, MODE, T>(bp, s);
+    default: return batched_main<512, 2, MODE, T>(bp, s);
     }
 }
 

@@ -2,6 +2,7 @@
 // kernels: launch parameter blocks, workspace layouts and launchers.
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -61,15 +62,14 @@ struct PolarParams {
 // Largest n a Polar stream accepts (keeps the tile budget arithmetic exact).
 constexpr int64_t kPolarMaxN = int64_t(1) << 48;
 
-// floor(sqrt(v)) for 0 <= v < 2^62, exact, in integers only.
+// floor(sqrt(v)) for 0 <= v < 2^62, exact: a double square root is within
+// one of the answer, and integer steps settle it.
 __host__ __device__ inline int64_t isqrt64(int64_t v)
 {
-    int64_t lo = 0, hi = int64_t(1) << 31;   // hi * hi > v
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) / 2;
-        if (mid * mid <= v) lo = mid; else hi = mid;
-    }
-    return lo;
+    int64_t r = (int64_t)sqrt((double)v);
+    while (r > 0 && r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
 }
 
 // Tile budget of a Polar stream of n outputs in tiles of `cand` candidates:

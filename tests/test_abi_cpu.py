@@ -113,7 +113,7 @@ def test_batched_workspace_size(lib):
     fixed = (64 + (k + 1) * 8 + k * 8 + k * 4 + 255) // 256 * 256
     # most slots over the configurations: the smallest Polar tile has 2*256*2 = 1024 candidates
     worst = 0
-    for threads, bpt in [(256, 2), (256, 4), (128, 4), (128, 2), (512, 2), (512, 1)]:
+    for threads, bpt in [(256, 4), (256, 8), (128, 8), (512, 4), (128, 4), (512, 2)]:
         cand = 2 * threads * bpt
         s = 0
         for n in (1000, 5000):

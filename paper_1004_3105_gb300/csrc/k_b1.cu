@@ -11,7 +11,7 @@
 
 namespace nrng {
 
-constexpr int kB1Threads = 256;
+constexpr int kB1Threads = 512;
 
 template <bool ALIGNED>
 __global__ void __launch_bounds__(kB1Threads)
@@ -33,32 +33,57 @@ k_uniform(float *__restrict__ out, int64_t n, int64_t nblocks, uint64_t counter,
     }
 }
 
+// Any n, any element alignment: the general kernel.
 template <int MODE, typename T, bool ALIGNED>
 __global__ void __launch_bounds__(kB1Threads)
 k_b1(T *__restrict__ out, int64_t n, int64_t nblocks, float mu, float sigma, uint64_t counter,
      const RoundKeys rk)
 {
     const int64_t stride = (int64_t)gridDim.x * kB1Threads;
-    // two independent blocks per iteration give the scheduler more to overlap
-    for (int64_t b = (int64_t)blockIdx.x * kB1Threads + threadIdx.x; b < nblocks; b += 2 * stride) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int64_t bq = b + q * stride;
-            if (bq >= nblocks) break;
-            const uint4 w = philox_block(counter + (uint64_t)bq, rk);
-            float x0, y0, x1, y1;
-            b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
-            b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
-            const int64_t i = 4 * bq;
-            if (ALIGNED && i + 4 <= n) {
-                store4_aligned(out + i, x0, y0, x1, y1);
-            } else {
-                if (i < n) store1(out + i, x0);
-                if (i + 1 < n) store1(out + i + 1, y0);
-                if (i + 2 < n) store1(out + i + 2, x1);
-                if (i + 3 < n) store1(out + i + 3, y1);
-            }
+    for (int64_t b = (int64_t)blockIdx.x * kB1Threads + threadIdx.x; b < nblocks; b += stride) {
+        const uint4 w = philox_block(counter + (uint64_t)b, rk);
+        float x0, y0, x1, y1;
+        b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
+        b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
+        const int64_t i = 4 * b;
+        if (ALIGNED && i + 4 <= n) {
+            store4_aligned(out + i, x0, y0, x1, y1);
+        } else {
+            if (i < n) store1(out + i, x0);
+            if (i + 1 < n) store1(out + i + 1, y0);
+            if (i + 2 < n) store1(out + i + 2, x1);
+            if (i + 3 < n) store1(out + i + 3, y1);
         }
+    }
+}
+
+// The common case: output aligned to 4 elements and fewer than 2^32 blocks.
+// The loop runs over whole blocks only, with 32-bit indices and the 64-bit
+// counter split into words; the last, partial block (n mod 4 outputs) is
+// done by one thread after it.
+template <int MODE, typename T>
+__global__ void __launch_bounds__(kB1Threads)
+k_b1_whole(T *__restrict__ out, int64_t n, uint32_t nwhole, float mu, float sigma, uint32_t c_lo,
+           uint32_t c_hi, const RoundKeys rk)
+{
+    const uint32_t stride = gridDim.x * kB1Threads;
+    for (uint32_t b = blockIdx.x * kB1Threads + threadIdx.x; b < nwhole; b += stride) {
+        const uint32_t lo = c_lo + b;
+        const uint32_t hi = c_hi + (lo < b ? 1u : 0u);
+        const uint4 w = philox4x32_10(lo, hi, rk);
+        float x0, y0, x1, y1;
+        b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
+        b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
+        store4_aligned(out + 4 * (size_t)b, x0, y0, x1, y1);
+    }
+    if ((n & 3) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint64_t c = ((uint64_t)c_hi << 32 | c_lo) + nwhole;
+        const uint4 w = philox_block(c, rk);
+        float v[4];
+        b1_pair<MODE>(w.x, w.y, mu, sigma, v[0], v[1]);
+        b1_pair<MODE>(w.z, w.w, mu, sigma, v[2], v[3]);
+        const int64_t i = 4 * (int64_t)nwhole;
+        for (int q = 0; q < 4 && i + q < n; ++q) store1(out + i + q, v[q]);
     }
 }
 
@@ -88,7 +113,11 @@ static void b1_dispatch_aligned(void *out, int64_t n, int64_t nblocks, float mu,
                                 uint64_t counter, const RoundKeys &rk, bool aligned, cudaStream_t s)
 {
     const int grid = b1_grid(nblocks);
-    if (aligned)
+    const int64_t nwhole = n / 4;
+    if (aligned && nwhole < (int64_t(1) << 32) - 2 * (int64_t)grid * kB1Threads)
+        k_b1_whole<MODE, T><<<grid, kB1Threads, 0, s>>>((T *)out, n, (uint32_t)nwhole, mu, sigma,
+                                                         (uint32_t)counter, (uint32_t)(counter >> 32), rk);
+    else if (aligned)
         k_b1<MODE, T, true><<<grid, kB1Threads, 0, s>>>((T *)out, n, nblocks, mu, sigma, counter, rk);
     else
         k_b1<MODE, T, false><<<grid, kB1Threads, 0, s>>>((T *)out, n, nblocks, mu, sigma, counter, rk);

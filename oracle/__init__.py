@@ -16,6 +16,10 @@ Functions and the passages they follow (paper: Brent, TR-CS-93-04, 1993):
   polar_accept_points
   lattice_accept_count           exact acceptance count of P's step 3
   batched                        independent B1/P streams
+  b3                             Sec. 3, Method B3 (exact function for h)
+  polar_p2                       Sec. 4, Method P2 (step 4a, exact function for h)
+  ratio, ratio_candidates,       Sec. 5, Algorithm R (ratio-of-uniforms region)
+  ratio_at
   reparam_fwd, reparam_bwd       x = mu + sigma z with z from B1, and its
                                  gradients (an add-on; no counterpart in the paper)
 """
@@ -71,6 +75,11 @@ def _load():
         "orc_polar_at": (None, [P, P, i64, f64, f64, u64, u64]),
         "orc_lattice_accept_count": (i64, []),
         "orc_batched": (None, [P, i32, P, P, P, P, P, P, P]),
+        "orc_b3": (None, [P, i64, f64, f64, u64, u64]),
+        "orc_polar_p2": (i64, [P, i64, f64, f64, u64, u64, P, P]),
+        "orc_ratio": (i64, [P, i64, f64, f64, u64, u64, P, P]),
+        "orc_ratio_candidates": (None, [P, i64, u64, u64]),
+        "orc_ratio_at": (None, [P, P, i64, f64, f64, u64, u64]),
         "orc_reparam_fwd": (None, [P, P, P, i64, i64, i64, u64, u64]),
         "orc_reparam_bwd": (None, [P, P, P, i64, i64, i64, u64, u64]),
     }
@@ -185,6 +194,46 @@ def polar_at(cand, mu: float, sigma: float, key: int, counter: int) -> np.ndarra
 
 def lattice_accept_count() -> int:
     return int(_load().orc_lattice_accept_count())
+
+
+def b3(n: int, mu: float, sigma: float, key: int, counter: int) -> np.ndarray:
+    """Method B3 (Sec. 3) with the exact sqrt(-ln(1-u)); n outputs."""
+    out = np.zeros(n, dtype=np.float64)
+    _load().orc_b3(_ptr(out), n, float(mu), float(sigma), _u64(key), _u64(counter))
+    return out
+
+
+def polar_p2(n: int, mu: float, sigma: float, key: int, counter: int):
+    """Method P2 (Sec. 4, step 4a); returns (out, pair_candidate, next_counter, candidates)."""
+    npairs = (n + 1) // 2
+    out = np.zeros(n, dtype=np.float64)
+    cand = np.zeros(npairs, dtype=np.int64)
+    nxt = np.zeros(1, dtype=np.uint64)
+    nc = _load().orc_polar_p2(_ptr(out), n, float(mu), float(sigma), _u64(key), _u64(counter), _ptr(cand),
+                              _ptr(nxt))
+    return out, cand, int(nxt[0]), int(nc)
+
+
+def ratio(n: int, mu: float, sigma: float, key: int, counter: int):
+    """Algorithm R (Sec. 5); returns (out, candidate per output, next_counter, candidates)."""
+    out = np.zeros(n, dtype=np.float64)
+    cand = np.zeros(n, dtype=np.int64)
+    nxt = np.zeros(1, dtype=np.uint64)
+    nc = _load().orc_ratio(_ptr(out), n, float(mu), float(sigma), _u64(key), _u64(counter), _ptr(cand), _ptr(nxt))
+    return out, cand, int(nxt[0]), int(nc)
+
+
+def ratio_candidates(ncand: int, key: int, counter: int) -> np.ndarray:
+    acc = np.zeros(ncand, dtype=np.uint8)
+    _load().orc_ratio_candidates(_ptr(acc), ncand, _u64(key), _u64(counter))
+    return acc
+
+
+def ratio_at(cand, mu: float, sigma: float, key: int, counter: int) -> np.ndarray:
+    cand = np.ascontiguousarray(cand, dtype=np.int64)
+    out = np.zeros(cand.size, dtype=np.float64)
+    _load().orc_ratio_at(_ptr(out), _ptr(cand), cand.size, float(mu), float(sigma), _u64(key), _u64(counter))
+    return out
 
 
 def batched(total: int, desc: dict) -> np.ndarray:

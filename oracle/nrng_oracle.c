@@ -19,6 +19,9 @@
  *   - Algorithm P (Polar): paper Sec. 2, steps 1-4; rejected pairs are
  *     compressed away in candidate order (the vector gather of Sec. 2 and the
  *     compress of Sec. 4, RANN3B).
+ *   - Method B3 (Sec. 3), Method P2 (Sec. 4, step 4a) and Algorithm R
+ *     (Sec. 5), each with the exact function where the paper fits a
+ *     polynomial;
  *   - the reparameterised sample x = mu + sigma*z and its gradients (an
  *     add-on: the paper has no autograd; z is B1's output).
  *
@@ -298,6 +301,142 @@ int64_t orc_lattice_accept_count(void)
         if (hi >= lo) total += hi - lo + 1;
     }
     return total - 1; /* the origin has s = 0 and is rejected */
+}
+
+/* ------------------------------------------------------- Method B3 (Sec 3) */
+
+/* Word i of the stream (block i/4, word i mod 4). */
+static uint32_t orc_word(int64_t i, uint64_t key, uint64_t counter)
+{
+    uint32_t w[4];
+    orc_block(key, counter, (uint64_t)(i / 4), w);
+    return w[i % 4];
+}
+
+/* Method B3, with the exact function in place of the paper's polynomial h:
+ *   step 1: u1, u2, u3 uniform (words 3p, 3p+1, 3p+2 of the stream for pair p);
+ *   step 2: m = max(u1, u2), u = m^2 (uniform on [0, 1));
+ *   step 3: r = sigma sqrt(-ln(1 - u));
+ *   step 4: s = sin(2 pi u3 - pi), c = cos(2 pi u3 - pi);
+ *   step 5: return mu + c r sqrt2 and mu + s r sqrt2 (out[2p], out[2p+1]). */
+void orc_b3(double *out, int64_t n, double mu, double sigma, uint64_t key, uint64_t counter)
+{
+    for (int64_t p = 0; 2 * p < n; ++p) {
+        double u1 = orc_u24(orc_word(3 * p, key, counter));
+        double u2 = orc_u24(orc_word(3 * p + 1, key, counter));
+        double u3 = orc_u24(orc_word(3 * p + 2, key, counter));
+        double m = (u1 > u2) ? u1 : u2;
+        double u = m * m;                       /* exact: m has 24 bits */
+        double r = sigma * sqrt(-log(1.0 - u));
+        double a = 2.0 * M_PI * u3 - M_PI;
+        out[2 * p] = mu + cos(a) * r * sqrt(2.0);
+        if (2 * p + 1 < n) out[2 * p + 1] = mu + sin(a) * r * sqrt(2.0);
+    }
+}
+
+/* ------------------------------------------------- Method P2 (Sec 4, 4a) */
+
+/* Step 4a with u = 1 - s (independent of the angle): r = sigma sqrt(-ln(1-s)/s),
+ * returning x r sqrt2 + mu, y r sqrt2 + mu.  The paper approximates
+ * sqrt(-ln(1-s)/s) by the polynomial h for s <= 8/9; the oracle evaluates it. */
+static void orc_p2_step4(int32_t kx, int32_t ky, double mu, double sigma, double *ox, double *oy)
+{
+    double x = (double)kx * 0x1p-23;
+    double y = (double)ky * 0x1p-23;
+    double s = x * x + y * y;
+    double r = sigma * sqrt(-log(1.0 - s) / s);
+    *ox = x * r * sqrt(2.0) + mu;
+    *oy = y * r * sqrt(2.0) + mu;
+}
+
+/* Method P2: the candidate stream, acceptance and compaction of Algorithm P,
+ * step 4 replaced by step 4a. */
+int64_t orc_polar_p2(double *out, int64_t n, double mu, double sigma, uint64_t key, uint64_t counter,
+                     int64_t *pair_cand, uint64_t *next_counter)
+{
+    int64_t npairs = (n + 1) / 2;
+    int64_t i = 0, c = 0, c_last = -1;
+    while (i < npairs) {
+        int32_t kx, ky;
+        orc_polar_candidate(c, key, counter, &kx, &ky);
+        if (orc_polar_accept(kx, ky)) {
+            double x, y;
+            orc_p2_step4(kx, ky, mu, sigma, &x, &y);
+            out[2 * i] = x;
+            if (2 * i + 1 < n) out[2 * i + 1] = y;
+            if (pair_cand) pair_cand[i] = c;
+            c_last = c;
+            ++i;
+        }
+        ++c;
+    }
+    if (next_counter)
+        *next_counter = (c_last < 0) ? counter : counter + (uint64_t)(c_last / 2) + 1u;
+    return c;
+}
+
+/* ------------------------------------------------ Algorithm R (Sec 5) ---- */
+
+/* Candidate c: u from word 2(c mod 2), v from word 2(c mod 2) + 1 of block c/2.
+ *   step 2: x = sqrt(8/e) (v - 1/2) / (1 - u);
+ *   step 3: reject unless x^2 <= -4 ln(1 - u) (the ratio-of-uniforms region;
+ *           see the reading of the printed condition in the design notes);
+ *   step 4: return sigma x + mu.
+ * All in double precision, the paper's. */
+static void orc_ratio_candidate(int64_t c, uint64_t key, uint64_t counter, double *u, double *v)
+{
+    uint32_t w[4];
+    orc_block(key, counter, (uint64_t)(c / 2), w);
+    int h = (int)(c % 2);
+    *u = orc_u24(w[2 * h]);
+    *v = orc_u24(w[2 * h + 1]);
+}
+
+static int orc_ratio_accept(double u, double v, double *x)
+{
+    *x = sqrt(8.0 / M_E) * (v - 0.5) / (1.0 - u);
+    return (*x) * (*x) <= -4.0 * log(1.0 - u);
+}
+
+int64_t orc_ratio(double *out, int64_t n, double mu, double sigma, uint64_t key, uint64_t counter,
+                  int64_t *cand_out, uint64_t *next_counter)
+{
+    int64_t i = 0, c = 0, c_last = -1;
+    while (i < n) {
+        double u, v, x;
+        orc_ratio_candidate(c, key, counter, &u, &v);
+        if (orc_ratio_accept(u, v, &x)) {
+            out[i] = sigma * x + mu;
+            if (cand_out) cand_out[i] = c;
+            c_last = c;
+            ++i;
+        }
+        ++c;
+    }
+    if (next_counter)
+        *next_counter = (c_last < 0) ? counter : counter + (uint64_t)(c_last / 2) + 1u;
+    return c;
+}
+
+void orc_ratio_candidates(uint8_t *accept, int64_t ncand, uint64_t key, uint64_t counter)
+{
+    for (int64_t c = 0; c < ncand; ++c) {
+        double u, v, x;
+        orc_ratio_candidate(c, key, counter, &u, &v);
+        accept[c] = (uint8_t)orc_ratio_accept(u, v, &x);
+    }
+}
+
+/* Step 2 and 4 of R at a chosen candidate (sampled checks). */
+void orc_ratio_at(double *out, const int64_t *cand, int64_t m, double mu, double sigma, uint64_t key,
+                  uint64_t counter)
+{
+    for (int64_t j = 0; j < m; ++j) {
+        double u, v, x;
+        orc_ratio_candidate(cand[j], key, counter, &u, &v);
+        orc_ratio_accept(u, v, &x);
+        out[j] = sigma * x + mu;
+    }
 }
 
 /* ------------------------------------------------------ batched streams -- */

@@ -300,7 +300,8 @@ class Step:
 
 
 def precision_sweep(step, K, W, peak):
-    """{B1, Polar} x {accurate, fast} x {f32, bf16, f16} at N = 2^28."""
+    """{B1, Polar} x {accurate, fast} x {f32, bf16, f16} at N = 2^28, then
+    Methods B2, B3, P2, R and the two-pass Polar in f32."""
     import torch
     nr = step.nr
     out = {}
@@ -328,6 +329,36 @@ def precision_sweep(step, K, W, peak):
                 gbs = by / (ms * 1e-3) / 1e9
                 out[f"{method}_{mode}_{names[dt]}"] = {"ms": round(ms, 4), "normals_per_s": N_FULL / (ms * 1e-3),
                                                        "GB_per_s": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4)}
+    # the paper's further methods and the two-pass Polar, f32, same N
+    ws_r = torch.empty(nr.nrng_ratio_workspace_size(N_FULL), dtype=torch.uint8, device=step.out_b1.device)
+    ws_2 = torch.empty(nr.nrng_polar_twopass_workspace_size(N_FULL), dtype=torch.uint8, device=step.out_b1.device)
+    buf = step.out_b1
+    variants = {
+        "b2_f32": lambda: nr.nrng_boxmuller(buf, 1.5, 0.25, KEY, step.base, "b2"),
+        "b3_f32": lambda: nr.nrng_boxmuller_b3(buf, 1.5, 0.25, KEY, step.base),
+        "p2_f32": lambda: nr.nrng_polar_p2(buf, 1.5, 0.25, KEY, step.base, step.ws_p),
+        "ratio_accurate_f32": lambda: nr.nrng_ratio(buf, 1.5, 0.25, KEY, step.base, ws_r, "accurate"),
+        "ratio_fast_f32": lambda: nr.nrng_ratio(buf, 1.5, 0.25, KEY, step.base, ws_r, "fast"),
+        "polar_twopass_accurate_f32": lambda: nr.nrng_polar_twopass(buf, 1.5, 0.25, KEY, step.base, ws_2, "accurate"),
+        "polar_twopass_fast_f32": lambda: nr.nrng_polar_twopass(buf, 1.5, 0.25, KEY, step.base, ws_2, "fast"),
+    }
+    for name, run in variants.items():
+        for _ in range(W):
+            run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        gbs = N_FULL * 4 / (ms * 1e-3) / 1e9
+        out[name] = {"ms": round(ms, 4), "normals_per_s": N_FULL / (ms * 1e-3), "GB_per_s": round(gbs, 1),
+                     "frac_of_hbm": round(gbs / peak, 4)}
+    for ws in (ws_r, ws_2):
+        st = nr.nrng_get_status(ws)
+        if st != 0:
+            raise RuntimeError(f"device status {nr._lib.STATUS.get(st, st)}")
     step.check_status()
     return out
 

@@ -64,11 +64,17 @@ typedef enum {
 
 typedef enum { NRNG_F32 = 0, NRNG_BF16 = 1, NRNG_F16 = 2 } nrng_dtype_t;
 
-/* NRNG_ACCURATE: log1pf/logf, sqrtf, IEEE division and sincospif.
- * NRNG_FAST: the hardware approximations (__logf, sqrt.approx, __sincosf)
- * with a short series for ln(1 - d) at small d, where the approximate log
- * loses relative accuracy. */
-typedef enum { NRNG_ACCURATE = 0, NRNG_FAST = 1 } nrng_mode_t;
+/* NRNG_ACCURATE: CUDA's correctly rounded or 1-ulp functions (log1pf and
+ *   sincospif for B1; logf of s held as an exact double-float, reciprocal and
+ *   sqrtf for P).  Error within 4e-6 max(1, |z|) of the FP64 definition.
+ * NRNG_FAST: the hardware approximations (log2, sqrt, rsqrt, sin, cos) with a
+ *   short series for ln(1 - d) at small d, where the approximate log loses
+ *   relative accuracy.  Error within 2e-5 max(1, |z|).
+ * NRNG_B2 (nrng_boxmuller only): the paper's Method B2 (Sec. 3), B1 with the
+ *   library ln and sqrt and an inline sine and cosine: polynomials at a
+ *   sixteenth of the angle and four double-angle steps.  Error within
+ *   2e-5 max(1, |z|). */
+typedef enum { NRNG_ACCURATE = 0, NRNG_FAST = 1, NRNG_B2 = 2 } nrng_mode_t;
 
 typedef enum { NRNG_B1 = 0, NRNG_POLAR = 1 } nrng_method_t;
 
@@ -135,6 +141,75 @@ int32_t nrng_polar(void *d_out, int64_t n, float mu, float sigma, uint64_t key,
                    uint64_t counter, int32_t dtype, int32_t mode, void *d_ws,
                    size_t ws_bytes, uint64_t *d_next_counter, int64_t *d_pair_candidate,
                    nrng_stream_t stream);
+
+/* Workspace bytes nrng_polar_twopass needs for n outputs. */
+int32_t nrng_polar_twopass_workspace_size(int64_t n, size_t *h_bytes);
+
+/* Polar, Algorithm P, with the compress done in two passes instead of one:
+ * a count pass draws every tile of candidates and counts the accepted ones,
+ * a scan turns the counts into each tile's first output pair, and a write
+ * pass draws each tile again and places its pairs there.  Arguments and
+ * outputs are those of nrng_polar, bit for bit (the same candidates, accept
+ * order and step-4 arithmetic); only the workspace size differs.  It is the
+ * two-pass alternative to nrng_polar's single-pass look-back (paper Sec. 4:
+ * the vector compress of RANN3B and the buffering of RANN3), kept for
+ * comparison.  Device errors (NRNG_ERR_EXHAUSTED) go to the status word. */
+int32_t nrng_polar_twopass(void *d_out, int64_t n, float mu, float sigma, uint64_t key,
+                           uint64_t counter, int32_t dtype, int32_t mode, void *d_ws,
+                           size_t ws_bytes, uint64_t *d_next_counter, int64_t *d_pair_candidate,
+                           nrng_stream_t stream);
+
+/* Box-Muller, Method B3 (paper Sec. 3): three uniforms per pair instead of
+ * two, so that no square root and, for most pairs, no logarithm is needed.
+ * Pair p takes words 3p, 3p + 1, 3p + 2 of the stream (word j is word
+ * j mod 4 of block counter + j/4), u_i = (w >> 8) 2^-24.  With
+ * m = max(u1, u2) and u = m^2 (uniform on [0, 1)), r = sigma sqrt(-ln(1 - u))
+ * is computed as sigma m h(v) by a fitted polynomial h of
+ * v = (6u - 4)/(4 - 3u) for u <= 8/9 and by logf above, and theta =
+ * 2 pi u3 - pi by Method B2's sine and cosine polynomials with double-angle
+ * steps.  d_out[2p] = sqrt(2) r cos(theta) + mu, d_out[2p + 1] =
+ * sqrt(2) r sin(theta) + mu.  Uses 3 ceil(n/8) blocks from `counter` (eight
+ * outputs per three blocks).  Single precision throughout; error within
+ * 2e-5 max(1, |z|) of the FP64 definition. */
+int32_t nrng_boxmuller_b3(void *d_out, int64_t n, float mu, float sigma, uint64_t key,
+                          uint64_t counter, int32_t dtype, nrng_stream_t stream);
+
+/* Polar, Method P2 (paper Sec. 4): Algorithm P's steps 1-3 (the same
+ * candidates, accept test and accept order as nrng_polar) and step 4a,
+ * r = sigma sqrt(-2 ln(1 - s) / s): the i-th accepted candidate gives
+ * d_out[2i] = r x + mu, d_out[2i + 1] = r y + mu.  1 - s is uniform and
+ * independent of the angle, so this is also a normal pair, different from
+ * nrng_polar's.  ln(1 - s)/s comes from the polynomial h of Method B3 for
+ * s <= 8/9 (no logarithm, no division) and from logf above.  Workspace,
+ * counter use, d_next_counter and d_pair_candidate: as nrng_polar (size it
+ * with nrng_polar_workspace_size).  Error within 2e-5 max(1, |z|). */
+int32_t nrng_polar_p2(void *d_out, int64_t n, float mu, float sigma, uint64_t key,
+                      uint64_t counter, int32_t dtype, void *d_ws, size_t ws_bytes,
+                      uint64_t *d_next_counter, int64_t *d_pair_candidate,
+                      nrng_stream_t stream);
+
+/* Workspace bytes nrng_ratio needs for n outputs.  Pure host computation. */
+int32_t nrng_ratio_workspace_size(int64_t n, size_t *h_bytes);
+
+/* The Ratio method, Algorithm R (paper Sec. 5; Kinderman and Monahan), one
+ * normal per accepted candidate, in candidate order.  Candidate c is block
+ * counter + c/2, words (u, v) = (w_{2h}, w_{2h+1}), h = c mod 2, on the
+ * 24-bit lattice.  x = sqrt(8/e) (v - 1/2) / (1 - u); accept iff
+ * x^2 <= -4 ln(1 - u) (the reading of the paper's step 3 under which the
+ * method yields N(0, 1); acceptance sqrt(pi e)/4 ~ 0.73).  The test is taken
+ * on the lattice as 2 a^2 <= e b^2 (-log1p(-u)) (a = v - 1/2, b = 1 - u in
+ * units of 2^-24): a float screen settles the clear cases and the rest is
+ * decided in double precision.  The i-th accepted candidate gives
+ * d_out[i] = sigma x + mu.
+ * d_ws/ws_bytes: at least nrng_ratio_workspace_size(n) bytes, cleared by this
+ *   call; it holds the status word afterwards.
+ * d_next_counter (nullable): counter + c_last/2 + 1.
+ * d_candidate (nullable): n int64, the candidate index of each output.
+ * mode: NRNG_ACCURATE (IEEE division) or NRNG_FAST (approximate division).
+ * Device errors (NRNG_ERR_TIMEOUT, NRNG_ERR_EXHAUSTED) go to the status word. */
+int32_t nrng_ratio(void *d_out, int64_t n, float mu, float sigma, uint64_t key,
+                   uint64_t counter, int32_t dtype, int32_t mode, void *d_ws, size_t ws_bytes,
+                   uint64_t *d_next_counter, int64_t *d_candidate, nrng_stream_t stream);
 
 /* Polar without a workspace, for callers that cannot allocate device memory
  * (no counterpart in the paper).  Some callers cannot obtain the workspace

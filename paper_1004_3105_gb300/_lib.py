@@ -47,6 +47,12 @@ SIGNATURES = {
     "nrng_polar_max_blocks": (_I32, [_I64, _PU64]),
     "nrng_polar": (_I32, [_P, _I64, _F32, _F32, _U64, _U64, _I32, _I32, _P, _SZ, _P, _P, _P]),
     "nrng_polar_noalloc": (_I32, [_P, _I64, _F32, _F32, _U64, _U64, _I32, _I32, _P, _P, _P, _P]),
+    "nrng_polar_twopass_workspace_size": (_I32, [_I64, _PSZ]),
+    "nrng_polar_twopass": (_I32, [_P, _I64, _F32, _F32, _U64, _U64, _I32, _I32, _P, _SZ, _P, _P, _P]),
+    "nrng_boxmuller_b3": (_I32, [_P, _I64, _F32, _F32, _U64, _U64, _I32, _P]),
+    "nrng_polar_p2": (_I32, [_P, _I64, _F32, _F32, _U64, _U64, _I32, _P, _SZ, _P, _P, _P]),
+    "nrng_ratio_workspace_size": (_I32, [_I64, _PSZ]),
+    "nrng_ratio": (_I32, [_P, _I64, _F32, _F32, _U64, _U64, _I32, _I32, _P, _SZ, _P, _P, _P]),
     "nrng_batched_workspace_size": (_I32, [_P, _I32, _PSZ]),
     "nrng_batched": (_I32, [_P, _P, _I32, _I32, _I32, _P, _SZ, _P]),
     "nrng_reparam_fwd": (_I32, [_P, _P, _P, _I64, _I64, _I64, _U64, _U64, _I32, _P]),

@@ -148,6 +148,8 @@ cudaError_t launch_b1(void *out, int64_t n, float mu, float sigma, uint64_t key,
     const RoundKeys rk = round_keys(key);
     if (mode == kModeFast)
         b1_dispatch_dtype<kModeFast>(out, n, nblocks, mu, sigma, counter, rk, dtype, aligned, s);
+    else if (mode == kModeB2)
+        b1_dispatch_dtype<kModeB2>(out, n, nblocks, mu, sigma, counter, rk, dtype, aligned, s);
     else
         b1_dispatch_dtype<kModeAccurate>(out, n, nblocks, mu, sigma, counter, rk, dtype, aligned, s);
     return cudaGetLastError();

@@ -12,7 +12,7 @@
 //     tile or one Polar tile (look-back within the stream's own status words).
 // Items of one stream are consecutive and handed out in increasing order, so
 // a Polar tile only waits on tiles already owned by running CTAs.  A Polar
-// tile taken after its stream is complete publishes a prefix of npairs and
+// tile taken after its stream is complete publishes a prefix of nitems and
 // returns, so that any later tile's look-back still terminates.
 #include <algorithm>
 #include <climits>
@@ -248,7 +248,7 @@ k_batched(BatchedParams bp)
         } else {
             PolarStream ps;
             ps.n = d.n;
-            ps.npairs = (d.n + 1) / 2;
+            ps.nitems = (d.n + 1) / 2;
             ps.mu = d.mu;
             ps.sigma = d.sigma;
             ps.counter = d.counter;
@@ -259,9 +259,9 @@ k_batched(BatchedParams bp)
             ps.pair_cand = nullptr;
             ps.silent_tile = -1;
             if (s_skip != 0) {
-                // Stream complete: every later tile's prefix is >= npairs.
+                // Stream complete: every later tile's prefix is >= nitems.
                 if (threadIdx.x == 0)
-                    st_relaxed(ps.status + t, kFlagPrefix | (unsigned long long)ps.npairs);
+                    st_relaxed(ps.status + t, kFlagPrefix | (unsigned long long)ps.nitems);
             } else if (((uintptr_t)out % (2 * sizeof(T))) == 0) {
                 ok = polar_tile<THREADS, BPT, MODE, T, true>(sm, out, ps, rk, t, bp.hdr, bp.spin_limit_ns);
             } else {

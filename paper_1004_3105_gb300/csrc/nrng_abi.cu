@@ -150,7 +150,7 @@ int32_t nrng_boxmuller(void *d_out, int64_t n, float mu, float sigma, uint64_t k
                        int32_t dtype, int32_t mode, nrng_stream_t stream)
 {
     if (n < 0 || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
-    if (!valid_dtype(dtype) || !valid_mode(mode)) return NRNG_ERR_INVALID_VALUE;
+    if (!valid_dtype(dtype) || !(valid_mode(mode) || mode == NRNG_B2)) return NRNG_ERR_INVALID_VALUE;
     if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
     if ((uintptr_t)d_out % dtype_size(dtype)) return NRNG_ERR_MISALIGNED;
     if (n == 0) return NRNG_OK;
@@ -196,7 +196,7 @@ int32_t nrng_polar(void *d_out, int64_t n, float mu, float sigma, uint64_t key, 
     PolarParams p;
     p.out = d_out;
     p.n = n;
-    p.npairs = (n + 1) / 2;
+    p.nitems = (n + 1) / 2;
     p.mu = mu;
     p.sigma = sigma;
     p.rk = round_keys(key);
@@ -211,6 +211,144 @@ int32_t nrng_polar(void *d_out, int64_t n, float mu, float sigma, uint64_t key, 
     p.spin_limit_ns = spin_limit_ns();
     const bool aligned = ((uintptr_t)d_out % (2 * dtype_size(dtype))) == 0;
     return cuda_status(launch_polar(p, dtype, mode, aligned, (cudaStream_t)stream), "nrng_polar");
+}
+
+int32_t nrng_polar_twopass_workspace_size(int64_t n, size_t *h_bytes)
+{
+    if (h_bytes == nullptr || n < 0 || n > kPolarMaxN) return NRNG_ERR_INVALID_VALUE;
+    *h_bytes = polar_twopass_workspace_bytes(n);
+    return NRNG_OK;
+}
+
+int32_t nrng_polar_twopass(void *d_out, int64_t n, float mu, float sigma, uint64_t key, uint64_t counter,
+                           int32_t dtype, int32_t mode, void *d_ws, size_t ws_bytes, uint64_t *d_next_counter,
+                           int64_t *d_pair_candidate, nrng_stream_t stream)
+{
+    if (n < 0 || n > kPolarMaxN || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
+    if (!valid_dtype(dtype) || !valid_mode(mode)) return NRNG_ERR_INVALID_VALUE;
+    if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
+    if ((uintptr_t)d_out % dtype_size(dtype) || (uintptr_t)d_ws % 256 || (uintptr_t)d_next_counter % 8 ||
+        (uintptr_t)d_pair_candidate % 8)
+        return NRNG_ERR_MISALIGNED;
+    if (n == 0) {
+        if (d_next_counter)
+            return cuda_status(launch_set_u64(d_next_counter, counter, (cudaStream_t)stream), "nrng_polar_twopass");
+        return NRNG_OK;
+    }
+    if (d_ws == nullptr || ws_bytes < polar_twopass_workspace_bytes(n)) return NRNG_ERR_WORKSPACE;
+    const uint64_t max_blocks = (uint64_t)polar_tiles_max(n) * kPolarBlocksPerTile;
+    if (!counter_fits(counter, max_blocks)) return NRNG_ERR_COUNTER_OVERFLOW;
+    PolarParams p;
+    p.out = d_out;
+    p.n = n;
+    p.nitems = (n + 1) / 2;
+    p.mu = mu;
+    p.sigma = sigma;
+    p.rk = round_keys(key);
+    p.counter = counter;
+    p.hdr = static_cast<WsHeader *>(d_ws);
+    p.tile_status = nullptr;
+    p.tiles_max = polar_tiles_max(n);
+    if (debug_polar_tiles() > 0 && debug_polar_tiles() < p.tiles_max) p.tiles_max = debug_polar_tiles();
+    p.next_counter = d_next_counter;
+    p.pair_cand = d_pair_candidate;
+    p.spin_limit_ns = spin_limit_ns();
+    p.debug_silent_tile = -1;
+    const bool aligned = ((uintptr_t)d_out % (2 * dtype_size(dtype))) == 0;
+    return cuda_status(launch_polar_twopass(p, dtype, mode, aligned, (cudaStream_t)stream), "nrng_polar_twopass");
+}
+
+int32_t nrng_boxmuller_b3(void *d_out, int64_t n, float mu, float sigma, uint64_t key, uint64_t counter,
+                          int32_t dtype, nrng_stream_t stream)
+{
+    if (n < 0 || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
+    if (!valid_dtype(dtype)) return NRNG_ERR_INVALID_VALUE;
+    if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
+    if ((uintptr_t)d_out % dtype_size(dtype)) return NRNG_ERR_MISALIGNED;
+    if (n == 0) return NRNG_OK;
+    if (n > (INT64_MAX / 3) || !counter_fits(counter, 3 * (uint64_t)((n + 7) / 8)))
+        return NRNG_ERR_COUNTER_OVERFLOW;
+    const bool aligned = ((uintptr_t)d_out % (4 * dtype_size(dtype))) == 0;
+    return cuda_status(launch_b3(d_out, n, mu, sigma, key, counter, dtype, aligned, (cudaStream_t)stream),
+                       "nrng_boxmuller_b3");
+}
+
+// Shared checks and parameters of the single-stream rejection calls (P2, R).
+static int32_t reject_params(PolarParams &p, void *d_out, int64_t n, int64_t nitems, float mu, float sigma,
+                             uint64_t key, uint64_t counter, int32_t dtype, void *d_ws, size_t ws_bytes,
+                             size_t ws_need, int64_t tiles, uint64_t *d_next_counter, int64_t *d_cand)
+{
+    if ((uintptr_t)d_out % dtype_size(dtype) || (uintptr_t)d_ws % 8 || (uintptr_t)d_next_counter % 8 ||
+        (uintptr_t)d_cand % 8)
+        return NRNG_ERR_MISALIGNED;
+    if (d_ws == nullptr || ws_bytes < ws_need) return NRNG_ERR_WORKSPACE;
+    if (!counter_fits(counter, (uint64_t)tiles * kPolarBlocksPerTile)) return NRNG_ERR_COUNTER_OVERFLOW;
+    p.out = d_out;
+    p.n = n;
+    p.nitems = nitems;
+    p.mu = mu;
+    p.sigma = sigma;
+    p.rk = round_keys(key);
+    p.counter = counter;
+    p.hdr = static_cast<WsHeader *>(d_ws);
+    p.tile_status = reinterpret_cast<unsigned long long *>(static_cast<char *>(d_ws) + sizeof(WsHeader));
+    p.tiles_max = tiles;
+    if (debug_polar_tiles() > 0 && debug_polar_tiles() < p.tiles_max) p.tiles_max = debug_polar_tiles();
+    p.debug_silent_tile = debug_silent_tile();
+    p.next_counter = d_next_counter;
+    p.pair_cand = d_cand;
+    p.spin_limit_ns = spin_limit_ns();
+    return NRNG_OK;
+}
+
+int32_t nrng_polar_p2(void *d_out, int64_t n, float mu, float sigma, uint64_t key, uint64_t counter,
+                      int32_t dtype, void *d_ws, size_t ws_bytes, uint64_t *d_next_counter,
+                      int64_t *d_pair_candidate, nrng_stream_t stream)
+{
+    if (n < 0 || n > kPolarMaxN || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
+    if (!valid_dtype(dtype)) return NRNG_ERR_INVALID_VALUE;
+    if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
+    if (n == 0) {
+        if ((uintptr_t)d_next_counter % 8) return NRNG_ERR_MISALIGNED;
+        if (d_next_counter)
+            return cuda_status(launch_set_u64(d_next_counter, counter, (cudaStream_t)stream), "nrng_polar_p2");
+        return NRNG_OK;
+    }
+    PolarParams p;
+    const int32_t st = reject_params(p, d_out, n, (n + 1) / 2, mu, sigma, key, counter, dtype, d_ws, ws_bytes,
+                                     polar_workspace_bytes(n), polar_tiles_max(n), d_next_counter,
+                                     d_pair_candidate);
+    if (st != NRNG_OK) return st;
+    const bool aligned = ((uintptr_t)d_out % (2 * dtype_size(dtype))) == 0;
+    return cuda_status(launch_polar_p2(p, dtype, aligned, (cudaStream_t)stream), "nrng_polar_p2");
+}
+
+int32_t nrng_ratio_workspace_size(int64_t n, size_t *h_bytes)
+{
+    if (h_bytes == nullptr || n < 0 || n > kPolarMaxN) return NRNG_ERR_INVALID_VALUE;
+    *h_bytes = ratio_workspace_bytes(n);
+    return NRNG_OK;
+}
+
+int32_t nrng_ratio(void *d_out, int64_t n, float mu, float sigma, uint64_t key, uint64_t counter, int32_t dtype,
+                   int32_t mode, void *d_ws, size_t ws_bytes, uint64_t *d_next_counter, int64_t *d_candidate,
+                   nrng_stream_t stream)
+{
+    if (n < 0 || n > kPolarMaxN || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
+    if (!valid_dtype(dtype) || !valid_mode(mode)) return NRNG_ERR_INVALID_VALUE;
+    if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
+    if (n == 0) {
+        if ((uintptr_t)d_next_counter % 8) return NRNG_ERR_MISALIGNED;
+        if (d_next_counter)
+            return cuda_status(launch_set_u64(d_next_counter, counter, (cudaStream_t)stream), "nrng_ratio");
+        return NRNG_OK;
+    }
+    PolarParams p;
+    const int32_t st = reject_params(p, d_out, n, n, mu, sigma, key, counter, dtype, d_ws, ws_bytes,
+                                     ratio_workspace_bytes(n), ratio_tiles_max(n), d_next_counter, d_candidate);
+    if (st != NRNG_OK) return st;
+    const bool aligned = ((uintptr_t)d_out % (2 * dtype_size(dtype))) == 0;
+    return cuda_status(launch_ratio(p, dtype, mode, aligned, (cudaStream_t)stream), "nrng_ratio");
 }
 
 int32_t nrng_batched_workspace_size(const nrng_stream_desc_t *h_desc, int32_t k, size_t *h_bytes)

@@ -13,6 +13,7 @@ namespace nrng {
 
 constexpr int kModeAccurate = NRNG_ACCURATE;
 constexpr int kModeFast = NRNG_FAST;
+constexpr int kModeB2 = NRNG_B2;
 constexpr int kStatusTimeout = NRNG_ERR_TIMEOUT;
 constexpr int kStatusExhausted = NRNG_ERR_EXHAUSTED;
 constexpr int kStatusInvalid = NRNG_ERR_INVALID_VALUE;
@@ -46,7 +47,7 @@ constexpr int kPolarCandPerTile = 2 * kPolarBlocksPerTile;      // 4096
 struct PolarParams {
     void *out;
     int64_t n;
-    int64_t npairs;
+    int64_t nitems;
     float mu, sigma;
     RoundKeys rk;
     uint64_t counter;
@@ -72,19 +73,34 @@ __host__ __device__ inline int64_t isqrt64(int64_t v)
     return r;
 }
 
-// Tile budget of a Polar stream of n outputs in tiles of `cand` candidates:
-// enough candidates that running out is a > 12-sigma binomial event (the
-// acceptance probability is pi/4 = 0.7854; the budget assumes 0.78), plus
-// one spare tile.  Integer-only, so host sizing and device checks agree.
+// Tile budget of a rejection stream that needs `items` accepted candidates,
+// in tiles of `cand` candidates accepted with probability at least pct/100:
+// enough candidates that running out is a > 12-sigma binomial event, plus one
+// spare tile.  Integer-only, so host sizing and device checks agree.
+__host__ __device__ inline int64_t reject_tiles_for(int64_t items, int64_t cand, int64_t pct)
+{
+    const int64_t need = items + 12 * (isqrt64(items) + 1) + 16;
+    return (need * 100 + cand * pct - 1) / (cand * pct) + 1;
+}
+
+// Polar (and P2): ceil(n/2) pairs, acceptance pi/4 = 0.7854, budgeted at 0.78.
 __host__ __device__ inline int64_t polar_tiles_for(int64_t n, int64_t cand)
 {
-    const int64_t npairs = (n + 1) / 2;
-    const int64_t need = npairs + 12 * (isqrt64(npairs) + 1) + 16;
-    return (need * 100 + cand * 78 - 1) / (cand * 78) + 1;
+    return reject_tiles_for((n + 1) / 2, cand, 78);
+}
+
+// Ratio method: n values, acceptance sqrt(pi e)/4 = 0.7306, budgeted at 0.72.
+__host__ __device__ inline int64_t ratio_tiles_for(int64_t n, int64_t cand)
+{
+    return reject_tiles_for(n, cand, 72);
 }
 
 int64_t polar_tiles_max(int64_t n);
 size_t polar_workspace_bytes(int64_t n);
+
+// Two-pass Polar (count pass, scan, write pass): header, int32 count and
+// int64 prefix per tile (prefix has tiles_max + 1 entries).
+size_t polar_twopass_workspace_bytes(int64_t n);
 
 // ------------------------------------------------------------- launchers --
 cudaError_t launch_uniform(float *out, int64_t n, uint64_t key, uint64_t counter, cudaStream_t s);
@@ -92,6 +108,15 @@ cudaError_t launch_b1(void *out, int64_t n, float mu, float sigma, uint64_t key,
                       int dtype, int mode, bool aligned, cudaStream_t s);
 cudaError_t launch_polar(const PolarParams &p, int dtype, int mode, bool aligned, cudaStream_t s);
 cudaError_t launch_set_u64(uint64_t *p, uint64_t v, cudaStream_t s);
+cudaError_t launch_polar_twopass(const PolarParams &p, int dtype, int mode, bool aligned, cudaStream_t s);
+
+// The paper's further methods (Sec. 3-5): B3, P2 and the Ratio method R.
+cudaError_t launch_b3(void *out, int64_t n, float mu, float sigma, uint64_t key, uint64_t counter, int dtype,
+                      bool aligned, cudaStream_t s);
+cudaError_t launch_polar_p2(const PolarParams &p, int dtype, bool aligned, cudaStream_t s);
+cudaError_t launch_ratio(const PolarParams &p, int dtype, int mode, bool aligned, cudaStream_t s);
+int64_t ratio_tiles_max(int64_t n);
+size_t ratio_workspace_bytes(int64_t n);
 
 // ---------------------------------------------------------------- reparam
 cudaError_t launch_reparam_fwd(float *x, const float *mu, const float *sigma, int64_t n, int64_t m,

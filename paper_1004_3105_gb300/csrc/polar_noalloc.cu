@@ -95,7 +95,7 @@ extern "C" int32_t nrng_polar_noalloc(void *d_out, int64_t n, float mu, float si
     PolarParams p;
     p.out = d_out;
     p.n = n;
-    p.npairs = (n + 1) / 2;
+    p.nitems = (n + 1) / 2;
     p.mu = mu;
     p.sigma = sigma;
     p.rk = round_keys(key);

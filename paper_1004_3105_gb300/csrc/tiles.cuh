@@ -61,9 +61,11 @@ __device__ __forceinline__ int total_of(const PolarSmem<THREADS, ROWS> &sm, int)
     return sm.total;
 }
 
-// Where a Polar stream's tile publishes and what it reports.
+// Where a rejection stream's tile publishes and what it reports.  nitems is
+// the number of accepted candidates the stream needs: ceil(n/2) pairs for
+// P and P2, n values for R.
 struct PolarStream {
-    int64_t n, npairs;
+    int64_t n, nitems;
     float mu, sigma;
     uint64_t counter;
     unsigned long long *status;   // this stream's tile status words
@@ -99,23 +101,93 @@ __device__ __forceinline__ void store_pair_bits(T *p, int2 v, bool both)
     }
 }
 
-// Tile t of a Polar stream: Algorithm P (Sec. 2, steps 1-4) on candidates
-// [t*kCand, (t+1)*kCand), in candidate order (row, warp, lane, half), with the
-// compress done per warp and a decoupled look-back across tiles.
-//   A  each warp draws its rows, tests 0 < S < 2^46 exactly, and appends its
-//      accepted points to its own shared-memory segment in candidate order
+// One output value (the Ratio method): bits of a float or a 16-bit value.
+template <typename T>
+__device__ __forceinline__ int2 item_bits(float z)
+{
+    if constexpr (sizeof(T) == 4) return make_int2(__float_as_int(z), 0);
+    else {
+        const T tz = OutTraits<T>::cvt(z);
+        uint16_t u;
+        memcpy(&u, &tz, 2);
+        return make_int2((int)u, 0);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_item_bits(T *p, int2 v)
+{
+    if constexpr (sizeof(T) == 4) *reinterpret_cast<int *>(p) = v.x;
+    else *reinterpret_cast<uint16_t *>(p) = (uint16_t)((unsigned)v.x & 0xFFFFu);
+}
+
+// ------------------------------------------------------------ policies ----
+// A rejection method on the candidate stream: each candidate is the two words
+// 2h, 2h+1 of a Philox block (h = 0, 1); accept() decides it and keeps a
+// payload, transform() turns an accepted payload into kOut output values.
+
+// Algorithm P (Sec. 2): payload (kx', ky'); steps 2-3 exact; step 4.
+template <int MODE>
+struct PolarPolicy {
+    static constexpr int kOut = 2;
+    __device__ static bool accept(uint32_t wa, uint32_t wb, int2 &pay)
+    {
+        const int32_t x = k24(wa), y = k24(wb);
+        pay = make_int2(x, y);
+        int64_t S;
+        return polar_accept(x, y, S);
+    }
+    __device__ static void transform(int2 p, float mu, float sigma, float &a, float &b)
+    {
+        polar_pair<MODE>(p.x, p.y, mu, sigma, a, b);
+    }
+};
+
+// Method P2 (Sec. 4): Algorithm P's steps 1-3, step 4a.
+struct P2Policy {
+    static constexpr int kOut = 2;
+    __device__ static bool accept(uint32_t wa, uint32_t wb, int2 &pay)
+    {
+        return PolarPolicy<kModeAccurate>::accept(wa, wb, pay);
+    }
+    __device__ static void transform(int2 p, float mu, float sigma, float &a, float &b)
+    {
+        p2_pair(p.x, p.y, mu, sigma, a, b);
+    }
+};
+
+// Algorithm R (Sec. 5): payload (a, b) of the lattice, one value per accept.
+template <int MODE>
+struct RatioPolicy {
+    static constexpr int kOut = 1;
+    __device__ static bool accept(uint32_t wu, uint32_t wv, int2 &pay) { return ratio_accept(wu, wv, pay); }
+    __device__ static void transform(int2 p, float mu, float sigma, float &a, float &b)
+    {
+        a = ratio_value<MODE>(p, mu, sigma);
+        b = 0.0f;
+    }
+};
+
+// Tile t of a rejection stream: the method's steps on candidates
+// [t*kCand, (t+1)*kCand) (Algorithm P, P2 or R by Policy), in candidate order
+// (row, warp, lane, half), with the compress done per warp and a decoupled
+// look-back across tiles.
+//   A  each warp draws its rows, runs the accept test, and appends the
+//      accepted payloads to its own shared-memory segment in candidate order
 //      (rank by ballot/popc); lane 0 records each (row, warp) count;
 //   B  warp 0 scans the counts and publishes the tile aggregate at once;
-//   C  each warp runs step 4 densely over its own segment, in place;
+//   C  each warp runs the transform densely over its own segment, in place;
 //   D  warp 0 looks back for the tile's exclusive prefix P;
-//   E  each warp copies its (row) runs to pairs P + offset(row, warp) + j,
-//      coalesced.
+//   E  each warp copies its (row) runs to items P + offset(row, warp) + j
+//      (elements kOut (P + ...)), coalesced.
 // Only A->B and D->E need the whole CTA; the rest is warp-synchronous.
 // Returns false when the look-back gave up (error recorded in hdr).
-template <int THREADS, int ROWS, int MODE, typename T, bool ALIGNED, typename Key>
-__device__ __forceinline__ bool polar_tile(PolarSmem<THREADS, ROWS> &sm, T *__restrict__ out,
-                                           const PolarStream &ps, const Key &rk, int64_t t, WsHeader *hdr,
-                                           unsigned long long limit_ns)
+// With KNOWN_PREFIX the tile's exclusive prefix is given (known_prefix, from
+// a count pass and a scan): nothing is published and nothing is awaited.
+template <class Policy, int THREADS, int ROWS, typename T, bool ALIGNED, typename Key, bool KNOWN_PREFIX = false>
+__device__ __forceinline__ bool reject_tile(PolarSmem<THREADS, ROWS> &sm, T *__restrict__ out,
+                                            const PolarStream &ps, const Key &rk, int64_t t, WsHeader *hdr,
+                                            unsigned long long limit_ns, long long known_prefix = 0)
 {
     constexpr int kWarps = THREADS / 32;
     constexpr int kEntries = ROWS * kWarps;
@@ -133,20 +205,19 @@ __device__ __forceinline__ bool polar_tile(PolarSmem<THREADS, ROWS> &sm, T *__re
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
         const uint4 w = philox_block(b0 + (uint64_t)(r * THREADS), rk);
-        const int32_t x0 = k24(w.x), y0 = k24(w.y), x1 = k24(w.z), y1 = k24(w.w);
-        int64_t S0, S1;
-        const bool a0 = polar_accept(x0, y0, S0);
-        const bool a1 = polar_accept(x1, y1, S1);
+        int2 p0, p1;
+        const bool a0 = Policy::accept(w.x, w.y, p0);
+        const bool a1 = Policy::accept(w.z, w.w, p1);
         const unsigned m0 = __ballot_sync(0xFFFFFFFFu, a0);
         const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1);
         const int pos = base + __popc(m0 & lt) + __popc(m1 & lt);
         const uint16_t c = (uint16_t)(2 * (r * THREADS + tid));
         if (a0) {
-            seg[pos] = make_int2(x0, y0);
+            seg[pos] = p0;
             cl[pos] = c;
         }
         if (a1) {
-            seg[pos + (a0 ? 1 : 0)] = make_int2(x1, y1);
+            seg[pos + (a0 ? 1 : 0)] = p1;
             cl[pos + (a0 ? 1 : 0)] = (uint16_t)(c + 1);
         }
         const int cnt = __popc(m0) + __popc(m1);
@@ -174,80 +245,82 @@ __device__ __forceinline__ bool polar_tile(PolarSmem<THREADS, ROWS> &sm, T *__re
         }
         if (lane == 0) {
             sm.total = total;
-            if (!silent)
+            if (!KNOWN_PREFIX && !silent)
                 st_relaxed(ps.status + t, (t == 0 ? kFlagPrefix : kFlagAggregate) | (unsigned long long)total);
         }
     }
 
-    // C: step 4 over this warp's segment, dense, results in place.
+    // C: the transform over this warp's segment, dense, results in place.
 #pragma unroll 1
     for (int j = lane; j < base; j += 32) {
-        const int2 k = seg[j];
-        float zx, zy;
-        polar_pair<MODE>(k.x, k.y, ps.mu, ps.sigma, zx, zy);
-        seg[j] = pair_bits<T>(zx, zy);
+        float za, zb;
+        Policy::transform(seg[j], ps.mu, ps.sigma, za, zb);
+        seg[j] = (Policy::kOut == 2) ? pair_bits<T>(za, zb) : item_bits<T>(za);
     }
 
     // D: warp 0 looks back for the exclusive prefix.
-    if (warp == 0) {
+    if (KNOWN_PREFIX) {
+        if (tid == 0) sm.prefix = known_prefix;
+    } else if (warp == 0) {
         const long long P = silent ? lookback_warp(ps.status, t, total, hdr, limit_ns, false, false)
                                    : lookback_warp(ps.status, t, total, hdr, limit_ns, false, true);
         if (lane == 0) {
             sm.prefix = P;
-            if (P >= 0 && t == ps.tiles_max - 1 && P + total < ps.npairs) raise_error(hdr, kStatusExhausted);
+            if (P >= 0 && t == ps.tiles_max - 1 && P + total < ps.nitems) raise_error(hdr, kStatusExhausted);
         }
     }
     __syncthreads();
 
-    // E: run r of this warp -> pairs P + off(r, warp) + j.
+    // E: run r of this warp -> items P + off(r, warp) + j.
+    constexpr int K = Policy::kOut;
     const long long P = sm.prefix;
     if (P < 0) return false;
-    if (P >= ps.npairs) return true;
-    if (ALIGNED && P + total_of(sm, kEntries) < ps.npairs && P + total_of(sm, kEntries) <= ps.n / 2 &&
-        ps.pair_cand == nullptr) {
-        // Every pair of the tile is placed whole and nothing else is recorded.
-        T *tile_out = out + 2 * P;
+    if (P >= ps.nitems) return true;
+    const int total_t = sm.total;
+    if (ALIGNED && P + total_t < ps.nitems && (K == 1 || P + total_t <= ps.n / 2) && ps.pair_cand == nullptr) {
+        // Every item of the tile is placed whole and nothing else is recorded.
+        T *tile_out = out + K * P;
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
             const int o = sm.off[r * kWarps + warp];
             const int rb = rowbase[r];
             const int cnt = rowbase[r + 1] - rb;
-            for (int j = lane; j < cnt; j += 32) store_pair_bits<T>(tile_out + 2 * (o + j), seg[rb + j], true);
+            for (int j = lane; j < cnt; j += 32) {
+                if (K == 2) store_pair_bits<T>(tile_out + 2 * (o + j), seg[rb + j], true);
+                else store_item_bits<T>(tile_out + (o + j), seg[rb + j]);
+            }
         }
         return true;
     }
-    const long long rem = ps.npairs - P;                 // pairs this tile may still place
-    const long long rem_full = ps.n / 2 - P;             // of which with both x and y
+    const long long rem = ps.nitems - P;                  // items this tile may still place
+    const long long rem_full = (K == 2) ? ps.n / 2 - P : rem;   // of which with every element
     const int lim = (int)(rem < kCand ? rem : kCand);
     const int lim_full = (int)(rem_full < kCand ? (rem_full > 0 ? rem_full : 0) : kCand);
-    T *tile_out = out + 2 * P;
+    T *tile_out = out + K * P;
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
         const int o = sm.off[r * kWarps + warp];
         const int cnt = rowbase[r + 1] - rowbase[r];
         for (int j = lane; j < cnt; j += 32) {
-            const int gl = o + j;   // pair index within the tile's output
+            const int gl = o + j;   // item index within the tile's output
             if (gl >= lim) break;
             const int2 v = seg[rowbase[r] + j];
-            if (ALIGNED) {
+            if (K == 1) {
+                store_item_bits<T>(tile_out + gl, v);
+            } else if (ALIGNED) {
                 store_pair_bits<T>(tile_out + 2 * gl, v, gl < lim_full);
+            } else if constexpr (sizeof(T) == 4) {
+                tile_out[2 * gl] = __int_as_float(v.x);
+                if (gl < lim_full) tile_out[2 * gl + 1] = __int_as_float(v.y);
             } else {
-                float zx, zy;
-                if constexpr (sizeof(T) == 4) {
-                    zx = __int_as_float(v.x);
-                    zy = __int_as_float(v.y);
-                    tile_out[2 * gl] = zx;
-                    if (gl < lim_full) tile_out[2 * gl + 1] = zy;
-                } else {
-                    const uint16_t lo = (uint16_t)((unsigned)v.x & 0xFFFFu), hi = (uint16_t)((unsigned)v.x >> 16);
-                    memcpy(&tile_out[2 * gl], &lo, 2);
-                    if (gl < lim_full) memcpy(&tile_out[2 * gl + 1], &hi, 2);
-                }
+                const uint16_t lo = (uint16_t)((unsigned)v.x & 0xFFFFu), hi = (uint16_t)((unsigned)v.x >> 16);
+                memcpy(&tile_out[2 * gl], &lo, 2);
+                if (gl < lim_full) memcpy(&tile_out[2 * gl + 1], &hi, 2);
             }
             if (ps.pair_cand || gl == lim - 1) {
                 const long long c = t * kCand + cl[rowbase[r] + j];
                 if (ps.pair_cand) ps.pair_cand[P + gl] = c;
-                if (P + gl == ps.npairs - 1) {
+                if (P + gl == ps.nitems - 1) {
                     if (ps.next_counter) *ps.next_counter = ps.counter + (uint64_t)(c / 2) + 1u;
                     st_relaxed_s32(ps.done, 1);
                 }
@@ -255,6 +328,59 @@ __device__ __forceinline__ bool polar_tile(PolarSmem<THREADS, ROWS> &sm, T *__re
         }
     }
     return true;
+}
+
+// Algorithm P's tile (the common case, for the single-stream and batched kernels).
+template <int THREADS, int ROWS, int MODE, typename T, bool ALIGNED, typename Key, bool KNOWN_PREFIX = false>
+__device__ __forceinline__ bool polar_tile(PolarSmem<THREADS, ROWS> &sm, T *__restrict__ out,
+                                           const PolarStream &ps, const Key &rk, int64_t t, WsHeader *hdr,
+                                           unsigned long long limit_ns, long long known_prefix = 0)
+{
+    return reject_tile<PolarPolicy<MODE>, THREADS, ROWS, T, ALIGNED, Key, KNOWN_PREFIX>(sm, out, ps, rk, t, hdr,
+                                                                                        limit_ns, known_prefix);
+}
+
+// One rejection stream over the whole grid: persistent CTAs take tile ids
+// from the workspace counter until the stream is complete (done) or the tile
+// budget is spent.
+template <class Policy, int MODE_OCC, typename T, bool ALIGNED>
+__global__ void __launch_bounds__(kPolarThreads, (PolarOccupancy<kPolarThreads, MODE_OCC>::kMinBlocks))
+k_reject(const PolarParams p)
+{
+    __shared__ PolarSmem<kPolarThreads, kPolarRows> sm;
+    __shared__ long long s_tile;
+
+    PolarStream ps;
+    ps.n = p.n;
+    ps.nitems = p.nitems;
+    ps.mu = p.mu;
+    ps.sigma = p.sigma;
+    ps.counter = p.counter;
+    ps.status = p.tile_status;
+    ps.tiles_max = p.tiles_max;
+    ps.done = &p.hdr->done;
+    ps.next_counter = p.next_counter;
+    ps.pair_cand = p.pair_cand;
+    ps.silent_tile = p.debug_silent_tile;
+    T *out = static_cast<T *>(p.out);
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            long long t = -1;
+            if (ld_relaxed_s32(&p.hdr->done) == 0) {
+                t = (long long)atomicAdd(&p.hdr->tile_counter, 1ull);
+                if (t >= p.tiles_max) t = -1;
+            }
+            s_tile = t;
+        }
+        __syncthreads();
+        const long long t = s_tile;
+        if (t < 0) break;
+        const bool ok = reject_tile<Policy, kPolarThreads, kPolarRows, T, ALIGNED>(sm, out, ps, p.rk, t, p.hdr,
+                                                                                 p.spin_limit_ns);
+        __syncthreads();
+        if (!ok) break;
+    }
 }
 
 }  // namespace nrng

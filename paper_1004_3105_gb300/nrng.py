@@ -16,9 +16,9 @@ import torch
 
 from ._lib import NrngError, check, load
 
-ACCURATE, FAST = 0, 1
+ACCURATE, FAST, B2 = 0, 1, 2
 B1, POLAR = 0, 1
-_MODES = {"accurate": ACCURATE, "fast": FAST, ACCURATE: ACCURATE, FAST: FAST}
+_MODES = {"accurate": ACCURATE, "fast": FAST, "b2": B2, ACCURATE: ACCURATE, FAST: FAST, B2: B2}
 _DTYPES = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
 
 # nrng_stream_desc_t, field for field (48 bytes).
@@ -31,7 +31,7 @@ def _mode(mode) -> int:
     try:
         return _MODES[mode]
     except KeyError:
-        raise ValueError(f"mode must be 'accurate' or 'fast', got {mode!r}") from None
+        raise ValueError(f"mode must be 'accurate', 'fast' or 'b2', got {mode!r}") from None
 
 
 def _dtype(t: torch.Tensor) -> int:
@@ -117,6 +117,84 @@ def nrng_polar(out: torch.Tensor, mu: float, sigma: float, key: int, counter: in
                             _dev(next_counter, "next_counter"), _dev(pair_candidate, "pair_candidate"),
                             _stream(stream)),
           "nrng_polar")
+
+
+def nrng_polar_twopass_workspace_size(n: int) -> int:
+    b = ctypes.c_size_t(0)
+    check(load().nrng_polar_twopass_workspace_size(int(n), ctypes.byref(b)), "nrng_polar_twopass_workspace_size")
+    return int(b.value)
+
+
+def nrng_polar_twopass(out: torch.Tensor, mu: float, sigma: float, key: int, counter: int, workspace: torch.Tensor,
+                       mode="accurate", next_counter: torch.Tensor = None, pair_candidate: torch.Tensor = None,
+                       stream=None) -> None:
+    """nrng_polar's outputs by a count pass, a scan and a write pass.
+    workspace: uint8 CUDA tensor of nrng_polar_twopass_workspace_size(n) bytes."""
+    n = out.numel()
+    if pair_candidate is not None and (pair_candidate.dtype != torch.int64 or pair_candidate.numel() < (n + 1) // 2):
+        raise ValueError("pair_candidate must be int64 with ceil(n/2) elements")
+    check(load().nrng_polar_twopass(_dev(out, "out"), n, float(mu), float(sigma), _u64(key), _u64(counter),
+                                    _dtype(out), _mode(mode), _dev(workspace, "workspace"),
+                                    workspace.numel() * workspace.element_size(), _dev(next_counter, "next_counter"),
+                                    _dev(pair_candidate, "pair_candidate"), _stream(stream)),
+          "nrng_polar_twopass")
+
+
+def _check_next_counter(next_counter):
+    if next_counter is not None and (next_counter.numel() < 1 or next_counter.element_size() != 8):
+        raise ValueError("next_counter must hold one 64-bit element")
+
+
+def _check_candidates(cand, need, name):
+    if cand is not None and (cand.dtype != torch.int64 or cand.numel() < need):
+        raise ValueError(f"{name} must be int64 with at least {need} elements")
+
+
+def nrng_boxmuller_b3(out: torch.Tensor, mu: float, sigma: float, key: int, counter: int, stream=None) -> None:
+    """Method B3: three uniforms per pair, h(v) for the radius, B2's sine and
+    cosine; fills `out` (uses 3 ceil(n/8) Philox blocks)."""
+    check(load().nrng_boxmuller_b3(_dev(out, "out"), out.numel(), float(mu), float(sigma), _u64(key),
+                                   _u64(counter), _dtype(out), _stream(stream)),
+          "nrng_boxmuller_b3")
+
+
+def nrng_polar_p2(out: torch.Tensor, mu: float, sigma: float, key: int, counter: int, workspace: torch.Tensor,
+                  next_counter: torch.Tensor = None, pair_candidate: torch.Tensor = None, stream=None) -> None:
+    """Method P2: Algorithm P's candidates and accept order, radius from 1 - s.
+    workspace: uint8 CUDA tensor of nrng_polar_workspace_size(n) bytes."""
+    n = out.numel()
+    _check_next_counter(next_counter)
+    _check_candidates(pair_candidate, (n + 1) // 2, "pair_candidate")
+    check(load().nrng_polar_p2(_dev(out, "out"), n, float(mu), float(sigma), _u64(key), _u64(counter), _dtype(out),
+                               _dev(workspace, "workspace"), workspace.numel() * workspace.element_size(),
+                               _dev(next_counter, "next_counter"), _dev(pair_candidate, "pair_candidate"),
+                               _stream(stream)),
+          "nrng_polar_p2")
+
+
+def nrng_ratio_workspace_size(n: int) -> int:
+    b = ctypes.c_size_t()
+    check(load().nrng_ratio_workspace_size(int(n), ctypes.byref(b)), "nrng_ratio_workspace_size")
+    return b.value
+
+
+def ratio_workspace(n: int, device=None) -> torch.Tensor:
+    """A device buffer of nrng_ratio_workspace_size(n) bytes (uint8)."""
+    return torch.empty(max(nrng_ratio_workspace_size(n), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def nrng_ratio(out: torch.Tensor, mu: float, sigma: float, key: int, counter: int, workspace: torch.Tensor,
+               mode="accurate", next_counter: torch.Tensor = None, candidate: torch.Tensor = None,
+               stream=None) -> None:
+    """Algorithm R (ratio of uniforms), one value per accepted candidate, in order.
+    candidate: optional int64 CUDA tensor of n elements (index of each output's candidate)."""
+    n = out.numel()
+    _check_next_counter(next_counter)
+    _check_candidates(candidate, n, "candidate")
+    check(load().nrng_ratio(_dev(out, "out"), n, float(mu), float(sigma), _u64(key), _u64(counter), _dtype(out),
+                            _mode(mode), _dev(workspace, "workspace"), workspace.numel() * workspace.element_size(),
+                            _dev(next_counter, "next_counter"), _dev(candidate, "candidate"), _stream(stream)),
+          "nrng_ratio")
 
 
 def nrng_polar_noalloc(out: torch.Tensor, mu: float, sigma: float, key: int, counter: int, mode="accurate",

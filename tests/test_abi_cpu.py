@@ -53,7 +53,8 @@ def test_boxmuller_validation(lib):
     assert f(FAKE, 5, float("nan"), 1.0, 1, 0, 0, 0, None) == _lib.ERR_INVALID_VALUE
     assert f(FAKE, 5, 0.0, float("inf"), 1, 0, 0, 0, None) == _lib.ERR_INVALID_VALUE
     assert f(FAKE, 5, 0.0, 1.0, 1, 0, 3, 0, None) == _lib.ERR_INVALID_VALUE      # dtype
-    assert f(FAKE, 5, 0.0, 1.0, 1, 0, 0, 2, None) == _lib.ERR_INVALID_VALUE      # mode
+    assert f(FAKE, 5, 0.0, 1.0, 1, 0, 0, 3, None) == _lib.ERR_INVALID_VALUE      # mode (2 = B2 is valid)
+    assert f(FAKE, 5, 0.0, 1.0, 1, 0, 0, -1, None) == _lib.ERR_INVALID_VALUE
     assert f(ODD, 5, 0.0, 1.0, 1, 0, 0, 0, None) == _lib.ERR_MISALIGNED
     assert f(ODD, 5, 0.0, 1.0, 1, 0, 1, 0, None) == _lib.ERR_MISALIGNED          # bf16 needs 2 bytes
     # ceil(9/4) = 3 blocks from 2^64 - 2 would pass 2^64
@@ -93,6 +94,53 @@ def test_polar_workspace_and_validation(lib):
         _lib.ERR_MISALIGNED
     assert f(FAKE, (1 << 48) + 1, 0.0, 1.0, 1, 0, 0, 0, FAKE, 1 << 40, None, None, None) == \
         _lib.ERR_INVALID_VALUE
+
+
+def test_b3_validation(lib):
+    f = lib.nrng_boxmuller_b3
+    assert f(None, 5, 0.0, 1.0, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, -1, 0.0, 1.0, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, 5, 0.0, -1.0, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, 5, 0.0, 1.0, 1, 0, 7, None) == _lib.ERR_INVALID_VALUE
+    assert f(ODD, 5, 0.0, 1.0, 1, 0, 2, None) == _lib.ERR_MISALIGNED
+    # 9 outputs take 3 ceil(9/8) = 6 blocks: from 2^64 - 5 they would pass 2^64
+    assert f(FAKE, 9, 0.0, 1.0, 1, 2 ** 64 - 5, 0, None) == _lib.ERR_COUNTER_OVERFLOW
+    assert f(FAKE, 0, 0.0, 1.0, 1, 0, 0, None) == _lib.OK
+
+
+def test_p2_validation(lib):
+    f = lib.nrng_polar_p2
+    assert f(FAKE, 100, 0.0, 1.0, 1, 0, 0, FAKE, 8, None, None, None) == _lib.ERR_WORKSPACE
+    assert f(FAKE, 100, 0.0, 1.0, 1, 0, 0, None, 1 << 20, None, None, None) == _lib.ERR_WORKSPACE
+    assert f(FAKE, 100, 0.0, 1.0, 1, 0, 9, FAKE, 1 << 20, None, None, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, 100, 0.0, float("nan"), 1, 0, 0, FAKE, 1 << 20, None, None, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, 100, 0.0, 1.0, 1, 2 ** 64 - 5, 0, FAKE, 1 << 20, None, None, None) == \
+        _lib.ERR_COUNTER_OVERFLOW
+    assert f(FAKE, 100, 0.0, 1.0, 1, 0, 0, FAKE, 1 << 20, ODD, None, None) == _lib.ERR_MISALIGNED
+    assert f(None, 0, 0.0, 1.0, 1, 0, 0, None, 0, None, None, None) == _lib.OK
+
+
+def test_ratio_workspace_and_validation(lib):
+    b = ctypes.c_size_t(0)
+    assert lib.nrng_ratio_workspace_size(-1, ctypes.byref(b)) == _lib.ERR_INVALID_VALUE
+    n = 1 << 28
+    assert lib.nrng_ratio_workspace_size(n, ctypes.byref(b)) == _lib.OK
+    # one word per tile of 4096 candidates at the 0.72 budget (acceptance sqrt(pi e)/4 = 0.7306)
+    tiles = (n + 12 * (int(np.sqrt(n)) + 1) + 16) * 100
+    tiles = (tiles + 4096 * 72 - 1) // (4096 * 72) + 1
+    assert b.value == (64 + 8 * tiles + 255) // 256 * 256
+    f = lib.nrng_ratio
+    assert f(FAKE, 100, 0.0, 1.0, 1, 0, 0, 0, FAKE, 8, None, None, None) == _lib.ERR_WORKSPACE
+    assert f(FAKE, 100, 0.0, 1.0, 1, 0, 0, 2, FAKE, 1 << 20, None, None, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, 100, 0.0, 1.0, 1, 0, 3, 0, FAKE, 1 << 20, None, None, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, 100, 0.0, -1.0, 1, 0, 0, 0, FAKE, 1 << 20, None, None, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, 100, 0.0, 1.0, 1, 2 ** 64 - 5, 0, 0, FAKE, 1 << 20, None, None, None) == \
+        _lib.ERR_COUNTER_OVERFLOW
+    assert f(ODD, 100, 0.0, 1.0, 1, 0, 1, 0, FAKE, 1 << 20, None, None, None) == _lib.ERR_MISALIGNED
+    assert f(FAKE, 100, 0.0, 1.0, 1, 0, 0, 0, FAKE, 1 << 20, None, ODD, None) == _lib.ERR_MISALIGNED
+    assert f(FAKE, (1 << 48) + 1, 0.0, 1.0, 1, 0, 0, 0, FAKE, 1 << 40, None, None, None) == \
+        _lib.ERR_INVALID_VALUE
+    assert f(None, 0, 0.0, 1.0, 1, 0, 0, 0, None, 0, None, None, None) == _lib.OK
 
 
 def _desc(ns, methods):

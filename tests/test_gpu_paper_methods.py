@@ -1,0 +1,185 @@
+"""GPU parity of the paper's further methods against the FP64 oracle, through
+the C ABI: Method B2 (Sec. 3; B1's definition, inline sine and cosine),
+Method B3 (Sec. 3), Method P2 (Sec. 4, step 4a) and the Ratio method R
+(Sec. 5).  Accept order, candidate indices and next_counter bit-exact; values
+within the fast-path tolerance (B2, B3, P2: polynomial approximations) or the
+accurate one (R: one division); every dtype, odd and tiny n, unaligned
+outputs; a full-size sample at 2^28; normality."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1004_3105_gb300 as nr
+from gpu_helpers import assert_canary, assert_close, canary_tensor, sync
+from paper_1004_3105_gb300 import workloads as W
+from stats import check_standard_normal_moments, ks_critical, ks_distance, normal_cdf
+
+pytestmark = pytest.mark.gpu
+DTYPES = [torch.float32, torch.bfloat16, torch.float16]
+SIZES = [(1, 0), (7, 0), (8, 0), (9, 1), (4097, 1), (100003, 0), (1 << 22, 0)]
+
+
+# ----------------------------------------------------------------------- B2
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,offset", [(1, 0), (5, 1), (65539, 0), (1 << 22, 0)])
+def test_b2_matches_b1_definition(dtype, n, offset):
+    mu, sigma = W.SWEEP_MU, W.SWEEP_SIGMA
+    whole, out = canary_tensor(n, dtype, offset=offset)
+    nr.nrng_boxmuller(out, mu, sigma, W.KEY_MAIN, 17, mode="b2")
+    sync()
+    assert_canary(whole, offset, n)
+    assert_close(out, oracle.boxmuller(n, mu, sigma, W.KEY_MAIN, 17), mu, sigma, "fast", f"B2 n={n}")
+
+
+def test_b2_sampled_2p24():
+    """2^24 outputs (about 2^23 angles, half the angle lattice's points on
+    average), checked at 2^18 sampled outputs against B1's definition."""
+    n = 1 << 24
+    out = torch.empty(n, device="cuda")
+    nr.nrng_boxmuller(out, 0.0, 1.0, 5, 0, mode="b2")
+    sync()
+    idx = W.sample_indices(n, 1 << 18)
+    assert_close(out[torch.from_numpy(idx).cuda()], oracle.boxmuller_at(idx, 0.0, 1.0, 5, 0), 0.0, 1.0, "fast",
+                 "B2 sampled")
+
+
+# ----------------------------------------------------------------------- B3
+def run_b3(n, mu, sigma, key, counter, dtype=torch.float32, offset=0):
+    whole, out = canary_tensor(n, dtype, offset=offset)
+    nr.nrng_boxmuller_b3(out, mu, sigma, key, counter)
+    sync()
+    assert_canary(whole, offset, n)
+    return out
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,offset", SIZES)
+def test_b3_oracle(dtype, n, offset):
+    mu, sigma = W.SWEEP_MU, W.SWEEP_SIGMA
+    out = run_b3(n, mu, sigma, W.KEY_MAIN, 21, dtype, offset)
+    assert_close(out, oracle.b3(n, mu, sigma, W.KEY_MAIN, 21), mu, sigma, "fast", f"B3 n={n}")
+
+
+def test_b3_full_size_sampled_groups():
+    """2^28 outputs; group g (outputs 8g .. 8g+7) is the oracle's stream
+    restarted at block counter + 3g, checked at sampled groups and the tail."""
+    n = 1 << 28
+    out = run_b3(n, 0.0, 1.0, W.KEY_MAIN, 0)
+    groups = np.unique(np.concatenate([W.sample_indices(n // 8, 4096), [n // 8 - 1]]))
+    got = out.view(-1, 8)[torch.from_numpy(groups).cuda()].reshape(-1)
+    ref = np.concatenate([oracle.b3(8, 0.0, 1.0, W.KEY_MAIN, 3 * int(g)) for g in groups])
+    assert_close(got, ref, 0.0, 1.0, "fast", "B3 2^28 sampled")
+
+
+def test_b3_normality():
+    n = 1_000_000
+    z = run_b3(n, 0.0, 1.0, 31337, 0).cpu().numpy().astype(np.float64)
+    check_standard_normal_moments(z)
+    assert ks_distance(z, normal_cdf) < ks_critical(n)
+
+
+# ----------------------------------------------------------------------- P2
+def run_p2(n, mu, sigma, key, counter, dtype=torch.float32, offset=0):
+    whole, out = canary_tensor(n, dtype, offset=offset)
+    ws = nr.polar_workspace(n)
+    nxt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cand = torch.full(((n + 1) // 2,), -1, dtype=torch.int64, device="cuda")
+    nr.nrng_polar_p2(out, mu, sigma, key, counter, ws, next_counter=nxt, pair_candidate=cand)
+    status = nr.nrng_get_status(ws)
+    assert status == 0, nr._lib.STATUS[status]
+    assert_canary(whole, offset, n)
+    return out, cand.cpu().numpy(), int(nxt.item()) & 0xFFFFFFFFFFFFFFFF
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,offset", SIZES)
+def test_p2_oracle(dtype, n, offset):
+    mu, sigma = W.SWEEP_MU, W.SWEEP_SIGMA
+    out, cand, nxt = run_p2(n, mu, sigma, W.KEY_MAIN, 5, dtype, offset)
+    ref, rcand, rnxt, _ = oracle.polar_p2(n, mu, sigma, W.KEY_MAIN, 5)
+    assert np.array_equal(cand, rcand), "accept order"
+    assert nxt == rnxt
+    assert_close(out, ref, mu, sigma, "fast", f"P2 n={n}")
+
+
+def test_p2_shares_polar_candidates():
+    n = 300001
+    _, cand, nxt = run_p2(n, 0.0, 1.0, 9, 0)
+    ws = nr.polar_workspace(n)
+    pc = torch.full(((n + 1) // 2,), -1, dtype=torch.int64, device="cuda")
+    pn = torch.zeros(1, dtype=torch.int64, device="cuda")
+    nr.nrng_polar(torch.empty(n, device="cuda"), 0.0, 1.0, 9, 0, ws, next_counter=pn, pair_candidate=pc)
+    assert nr.nrng_get_status(ws) == 0
+    assert np.array_equal(cand, pc.cpu().numpy()) and nxt == int(pn.item())
+
+
+def test_p2_normality():
+    n = 1_000_000
+    out, _, _ = run_p2(n, 0.0, 1.0, 4242, 0)
+    z = out.cpu().numpy().astype(np.float64)
+    check_standard_normal_moments(z)
+    assert ks_distance(z, normal_cdf) < ks_critical(n)
+
+
+# ------------------------------------------------------------------------ R
+def run_ratio(n, mu, sigma, key, counter, mode="accurate", dtype=torch.float32, offset=0):
+    whole, out = canary_tensor(n, dtype, offset=offset)
+    ws = nr.ratio_workspace(n)
+    nxt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cand = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+    nr.nrng_ratio(out, mu, sigma, key, counter, ws, mode, next_counter=nxt, candidate=cand)
+    status = nr.nrng_get_status(ws)
+    assert status == 0, nr._lib.STATUS[status]
+    assert_canary(whole, offset, n)
+    return out, cand.cpu().numpy(), int(nxt.item()) & 0xFFFFFFFFFFFFFFFF
+
+
+@pytest.mark.parametrize("mode", ["accurate", "fast"])
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,offset", SIZES)
+def test_ratio_oracle(mode, dtype, n, offset):
+    mu, sigma = W.SWEEP_MU, W.SWEEP_SIGMA
+    out, cand, nxt = run_ratio(n, mu, sigma, W.KEY_MAIN, 13, mode, dtype, offset)
+    ref, rcand, rnxt, _ = oracle.ratio(n, mu, sigma, W.KEY_MAIN, 13)
+    assert np.array_equal(cand, rcand), "accept order"
+    assert nxt == rnxt
+    assert_close(out, ref, mu, sigma, "accurate" if mode == "accurate" else "fast", f"R {mode} n={n}")
+
+
+def test_ratio_full_size_accept_order_and_sample():
+    """2^28 outputs: every candidate index against the oracle's accept bits,
+    values at sampled outputs."""
+    n = 1 << 28
+    out, cand, nxt = run_ratio(n, 0.0, 1.0, W.KEY_MAIN, 0)
+    ncand = int(cand[-1]) + 1
+    acc = oracle.ratio_candidates(ncand, W.KEY_MAIN, 0)
+    assert np.array_equal(np.flatnonzero(acc), cand)
+    assert nxt == int(cand[-1]) // 2 + 1
+    idx = W.sample_indices(n, 1 << 16)
+    assert_close(out[torch.from_numpy(idx).cuda()], oracle.ratio_at(cand[idx], 0.0, 1.0, W.KEY_MAIN, 0),
+                 0.0, 1.0, "accurate", "R 2^28 sampled")
+
+
+def test_ratio_continuation():
+    n1, n2 = 10001, 7000
+    _, _, nxt = run_ratio(n1, 0.0, 1.0, 77, 5)
+    assert nxt == oracle.ratio(n1, 0.0, 1.0, 77, 5)[2]
+    out2, _, _ = run_ratio(n2, 0.0, 1.0, 77, nxt)
+    assert_close(out2, oracle.ratio(n2, 0.0, 1.0, 77, nxt)[0], 0.0, 1.0, "accurate", "R continuation")
+
+
+def test_ratio_zero_n_sets_next_counter():
+    nxt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    nr.nrng_ratio(torch.empty(0, device="cuda"), 0.0, 1.0, 1, 999, nr.ratio_workspace(1), next_counter=nxt)
+    sync()
+    assert int(nxt.item()) == 999
+
+
+@pytest.mark.parametrize("mode", ["accurate", "fast"])
+def test_ratio_normality(mode):
+    n = 1_000_000
+    out, _, _ = run_ratio(n, 0.0, 1.0, 2718, 0, mode)
+    z = out.cpu().numpy().astype(np.float64)
+    check_standard_normal_moments(z)
+    assert ks_distance(z, normal_cdf) < ks_critical(n)

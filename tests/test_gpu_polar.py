@@ -105,3 +105,31 @@ def test_polar_repeat_is_deterministic():
     a, ca, na = run_polar(n, 0.0, 1.0, 9, 0, "fast")
     b, cb, nb = run_polar(n, 0.0, 1.0, 9, 0, "fast")
     assert torch.equal(a, b) and np.array_equal(ca, cb) and na == nb
+
+
+@pytest.mark.parametrize("mode", ["accurate", "fast"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("n,offset", [(1, 0), (4097, 1), (100003, 0), (1 << 22, 0)])
+def test_polar_twopass_equals_single_pass(mode, dtype, n, offset):
+    """The count/scan/write form gives nrng_polar's outputs bit for bit."""
+    mu, sigma = W.SWEEP_MU, W.SWEEP_SIGMA
+    one, cand1, nxt1 = run_polar(n, mu, sigma, W.KEY_MAIN, 9, mode, dtype, offset)
+    whole, out = canary_tensor(n, dtype, offset=offset)
+    ws = torch.empty(nr.nrng_polar_twopass_workspace_size(n), dtype=torch.uint8, device="cuda")
+    nxt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cand = torch.full(((n + 1) // 2,), -1, dtype=torch.int64, device="cuda")
+    nr.nrng_polar_twopass(out, mu, sigma, W.KEY_MAIN, 9, ws, mode, next_counter=nxt, pair_candidate=cand)
+    assert nr.nrng_get_status(ws) == 0
+    assert_canary(whole, offset, n)
+    assert torch.equal(out, one)
+    assert np.array_equal(cand.cpu().numpy(), cand1)
+    assert int(nxt.item()) == nxt1
+
+
+def test_polar_twopass_oracle_and_budget():
+    n = 300001
+    ws = torch.empty(nr.nrng_polar_twopass_workspace_size(n), dtype=torch.uint8, device="cuda")
+    out = torch.empty(n, device="cuda")
+    nr.nrng_polar_twopass(out, 0.0, 1.0, 5, 0, ws, "accurate")
+    assert nr.nrng_get_status(ws) == 0
+    assert_close(out, oracle.polar(n, 0.0, 1.0, 5, 0)[0], 0.0, 1.0, "accurate", "twopass")

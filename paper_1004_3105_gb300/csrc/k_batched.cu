@@ -5,15 +5,22 @@
 // and buffers the variable output of its vector Polar kernel (Sec. 4,
 // RANN3/RANN3B).  Here thousands of uneven streams share one grid:
 //   k_batched_prep (one CTA) validates the descriptors, turns each stream into
-//     a number of tiles (its work items) and scans them, together with the
-//     Polar streams' tile status slots, into the workspace;
+//     work items and scans them, together with the Polar streams' tile status
+//     slots, into the workspace.  A B1 stream's items are its tiles; a Polar
+//     stream's are its expected number of tiles (primary items) plus one
+//     overflow item, placed after every stream's primary items, that runs
+//     whatever tiles the stream still needs, one after another;
 //   k_batched (persistent, one global work counter) pulls items in order,
-//     finds the stream by binary search over the item prefix and runs one B1
-//     tile or one Polar tile (look-back within the stream's own status words).
-// Items of one stream are consecutive and handed out in increasing order, so
-// a Polar tile only waits on tiles already owned by running CTAs.  A Polar
-// tile taken after its stream is complete publishes a prefix of nitems and
-// returns, so that any later tile's look-back still terminates.
+//     finds the stream by a galloping search over the item prefix and runs a
+//     B1 tile or Polar tiles (look-back within the stream's own status words).
+// Items are handed out in increasing order, a CTA starts an item as soon as
+// it has claimed it, and a stream's tiles are claimed in increasing tile
+// order, so a Polar tile only waits on tiles already owned by running CTAs.
+// (Claiming the next item while the current one runs was measured: it lets
+// a claimed tile start up to a tile later than its successors, which then
+// wait in their look-back, and the whole batch ran twice as long.)  A Polar tile taken after its stream is
+// complete publishes a prefix of nitems and returns, so that any later tile's
+// look-back still ends.
 #include <algorithm>
 #include <climits>
 
@@ -40,6 +47,23 @@ __host__ __device__ inline int64_t b1_items(int64_t n, int64_t tile_blocks)
     return (nblocks + tile_blocks - 1) / tile_blocks;
 }
 
+// A Polar stream's primary tiles: the expected number of tiles its pairs
+// need at acceptance pi/4, ceil(nitems / (cand 0.7854)), at least one and at
+// most the tile budget.  They are its work items in the stream-ordered part
+// of the item space; whatever the stream still needs after them (a fraction
+// of a tile, at most a few) its overflow item takes, in the part of the item
+// space claimed after every primary tile.  Items for the whole tile budget
+// would spend the budget's margin (the 12-sigma excess and the extra tile)
+// on fully drawn tiles that are not needed, most of the work of a short
+// stream.
+__host__ __device__ inline int64_t polar_primary_tiles(int64_t n, int64_t cand)
+{
+    const int64_t nitems = (n + 1) / 2;
+    const int64_t t = (nitems * 10000 + cand * 7854 - 1) / (cand * 7854);
+    const int64_t budget = polar_tiles_for(n, cand);
+    return t < 1 ? 1 : (t > budget ? budget : t);
+}
+
 // Items and status slots of one stream; -1 items marks an invalid descriptor,
 // -2 a counter that would pass 2^64.
 __host__ __device__ inline void stream_items(const nrng_stream_desc_t &d, int threads, int bpt,
@@ -60,9 +84,9 @@ __host__ __device__ inline void stream_items(const nrng_stream_desc_t &d, int th
         const uint64_t blocks = (uint64_t)((d.n + 3) / 4);
         if (d.counter > ULLONG_MAX - (blocks - 1)) items = -2;
     } else {
-        items = polar_tiles_for(d.n, 2 * tile_blocks);
-        slots = items;
-        const uint64_t blocks = (uint64_t)(items * tile_blocks);
+        slots = polar_tiles_for(d.n, 2 * tile_blocks);
+        items = polar_primary_tiles(d.n, 2 * tile_blocks);
+        const uint64_t blocks = (uint64_t)(slots * tile_blocks);
         if (d.counter > ULLONG_MAX - (blocks - 1)) items = -2;
     }
 }
@@ -149,13 +173,15 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
         const size_t need = batched_layout(bp.k).tile_status + (size_t)cs * 8;
         int bad = s_bad;
         if (!bad && need > bp.ws_bytes) bad = kStatusWorkspace;
-        if (!bad && ci >= (1ll << 31)) bad = kStatusInvalid;   // item ids are 32-bit
         if (bad) {
             bp.hdr->status = bad;
             bp.hdr->done = 1;
             bp.hdr->aux[0] = 0;
+            bp.hdr->aux[1] = 0;
         } else {
-            bp.hdr->aux[0] = (unsigned long long)ci;
+            // primary items, then one overflow item per stream
+            bp.hdr->aux[0] = (unsigned long long)ci + (unsigned long long)bp.k;
+            bp.hdr->aux[1] = (unsigned long long)ci;
         }
     }
 }
@@ -163,89 +189,106 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
 // ------------------------------------------------------------ main --------
 // The batched kernel carries both tile bodies (B1 and Polar), so it is
 // compiled for fewer resident threads than the single-stream Polar kernel
-// (768 per SM, about 85 registers a thread).
+// (1024 per SM, 64 registers a thread).
 template <int THREADS, int MODE>
 struct BatchedOccupancy {
-    static constexpr int kThreads = 768;
+    static constexpr int kThreads = 1024;
     static constexpr int kMinBlocks = (kThreads / THREADS) > 0 ? (kThreads / THREADS) : 1;
 };
 
-// Streams whose item prefix is cached in shared memory (as int32) for the
-// item -> stream search; more streams fall back to searching global memory.
-constexpr int kSmemStreams = 8192;
+// One unit of work of a CTA: tiles [t0, t1) of stream `stream` (-1: none left).
+struct BatchedWork {
+    nrng_stream_desc_t d;
+    long long t0, t1;
+    int stream;
+    int skip;       // Polar stream complete when claimed
+    int overflow;   // the stream's overflow item
+};
+
+// Claims the next item and resolves it to a stream and tile range (one
+// thread).  Items [0, primary) are the streams' primary tiles in stream
+// order; item primary + j is stream j's overflow item.  `last` is the stream
+// of this CTA's previous primary item: items only increase, so the search
+// gallops up from it.
+__device__ __forceinline__ void batched_claim(const BatchedParams &bp, unsigned long long total_items,
+                                              unsigned long long primary, int cand, int &last, BatchedWork &w)
+{
+    long long item = -1;
+    if (ld_relaxed_s32(&bp.hdr->done) == 0) {
+        const unsigned long long it = atomicAdd(&bp.hdr->tile_counter, 1ull);
+        if (it < total_items) item = (long long)it;
+    }
+    if (item < 0) {
+        w.stream = -1;
+        return;
+    }
+    int j;
+    if ((unsigned long long)item < primary) {
+        // largest j with item_prefix[j] <= item (empty streams share a prefix
+        // with the next one; the largest j is the non-empty one)
+        int lo = last, step = 1, hi;
+        for (;;) {
+            hi = lo + step;
+            if (hi >= bp.k) { hi = bp.k; break; }
+            if (bp.item_prefix[hi] > item) break;
+            lo = hi;
+            step <<= 1;
+        }
+        while (hi - lo > 1) {   // prefix[lo] <= item < prefix[hi]
+            const int mid = (lo + hi) >> 1;
+            if (bp.item_prefix[mid] <= item) lo = mid; else hi = mid;
+        }
+        j = lo;
+        last = lo;
+        w.t0 = item - bp.item_prefix[j];
+        w.t1 = w.t0 + 1;
+        w.overflow = 0;
+    } else {
+        j = (int)(item - (long long)primary);
+        w.t0 = bp.item_prefix[j + 1] - bp.item_prefix[j];   // the stream's primary tiles
+        w.overflow = 1;
+    }
+    w.d = bp.desc[j];
+    const bool polar = (w.d.method == NRNG_POLAR);
+    if (w.overflow) w.t1 = polar ? polar_tiles_for(w.d.n, cand) : w.t0;   // B1 has no overflow
+    w.skip = polar ? ld_relaxed_s32(bp.stream_done + j) : 0;
+    w.stream = j;
+}
 
 template <int THREADS, int BPT, int MODE, typename T>
 __global__ void __launch_bounds__(THREADS, (BatchedOccupancy<THREADS, MODE>::kMinBlocks))
 k_batched(BatchedParams bp)
 {
+    constexpr int kCand = 2 * THREADS * BPT;
     __shared__ PolarSmem<THREADS, BPT> sm;
-    __shared__ long long s_item;
-    __shared__ int s_stream;
-    __shared__ int s_skip;
-    __shared__ nrng_stream_desc_t s_desc;
-    extern __shared__ int s_prefix[];   // item_prefix[0..k] when k <= kSmemStreams
+    __shared__ BatchedWork s_work;
+    __shared__ int s_done;
 
     const unsigned long long total_items = bp.hdr->aux[0];
-    const bool cached = bp.k <= kSmemStreams;
-    if (cached) {
-        for (int j = threadIdx.x; j <= bp.k; j += THREADS) s_prefix[j] = (int)bp.item_prefix[j];
-        __syncthreads();
-    }
+    const unsigned long long primary = bp.hdr->aux[1];
     char *out_base = static_cast<char *>(bp.out);
-    int last = 0;   // thread 0: stream of the previous item (items only increase)
+    int last = 0;   // thread 0: stream of the previous primary item
     for (;;) {
-        if (threadIdx.x == 0) {
-            long long item = -1;
-            if (ld_relaxed_s32(&bp.hdr->done) == 0) {
-                const unsigned long long it = atomicAdd(&bp.hdr->tile_counter, 1ull);
-                if (it < total_items) item = (long long)it;
-            }
-            int j = -1;
-            if (item >= 0) {
-                // largest j with item_prefix[j] <= item: gallop up from the
-                // previous stream, then bisect (empty streams share a prefix
-                // with the next one; the largest j is the non-empty one)
-                const int it32 = (int)item;
-                int lo = last, step = 1, hi;
-                for (;;) {
-                    hi = lo + step;
-                    if (hi >= bp.k) { hi = bp.k; break; }
-                    const int v = cached ? s_prefix[hi] : (int)bp.item_prefix[hi];
-                    if (v > it32) break;
-                    lo = hi;
-                    step <<= 1;
-                }
-                while (hi - lo > 1) {   // prefix[lo] <= item < prefix[hi]
-                    const int mid = (lo + hi) >> 1;
-                    const int v = cached ? s_prefix[mid] : (int)bp.item_prefix[mid];
-                    if (v <= it32) lo = mid; else hi = mid;
-                }
-                j = lo;
-                last = lo;
-                s_desc = bp.desc[j];
-            }
-            s_item = item;
-            s_stream = j;
-            // One thread reads the stream's completion flag for the whole CTA:
-            // every thread must take the same branch around polar_tile's
-            // barriers and full-warp ballots.
-            s_skip = (j >= 0 && s_desc.method == NRNG_POLAR) ? ld_relaxed_s32(bp.stream_done + j) : 0;
-        }
+        if (threadIdx.x == 0) batched_claim(bp, total_items, primary, kCand, last, s_work);
         __syncthreads();
-        const long long item = s_item;
-        if (item < 0) break;
-        const int j = s_stream;
-        const nrng_stream_desc_t d = s_desc;
-        const int64_t t = item - (cached ? (long long)s_prefix[j] : bp.item_prefix[j]);
-        const StreamKey rk{(uint32_t)d.key, (uint32_t)(d.key >> 32)};
+        const int j = s_work.stream;
+        if (j < 0) break;
+        const nrng_stream_desc_t d = s_work.d;
+        const long long t0 = s_work.t0, t1 = s_work.t1;
+        const bool overflow = s_work.overflow != 0;
+        int skip = s_work.skip;
+        RoundKeys rk;
+        make_round_keys(d.key, rk);
         T *out = reinterpret_cast<T *>(out_base) + d.offset;
         bool ok = true;
         if (d.method == NRNG_B1) {
-            if (((uintptr_t)out % (4 * sizeof(T))) == 0)
-                b1_tile<THREADS, BPT, MODE, T, true>(out, d.n, d.mu, d.sigma, rk, d.counter, t);
+            if (overflow) {
+                // B1 streams have no overflow tiles
+            } else if (((uintptr_t)out % (4 * sizeof(T))) == 0)
+                b1_tile<THREADS, BPT, MODE, T, true>(out, d.n, d.mu, d.sigma, rk, d.counter, t0);
             else
-                b1_tile<THREADS, BPT, MODE, T, false>(out, d.n, d.mu, d.sigma, rk, d.counter, t);
-        } else {
+                b1_tile<THREADS, BPT, MODE, T, false>(out, d.n, d.mu, d.sigma, rk, d.counter, t0);
+        } else if (!(overflow && skip)) {
             PolarStream ps;
             ps.n = d.n;
             ps.nitems = (d.n + 1) / 2;
@@ -253,19 +296,31 @@ k_batched(BatchedParams bp)
             ps.sigma = d.sigma;
             ps.counter = d.counter;
             ps.status = bp.tile_status + bp.slot_base[j];
-            ps.tiles_max = polar_tiles_for(d.n, 2 * THREADS * BPT);
+            ps.tiles_max = polar_tiles_for(d.n, kCand);
             ps.done = bp.stream_done + j;
             ps.next_counter = nullptr;
             ps.pair_cand = nullptr;
             ps.silent_tile = -1;
-            if (s_skip != 0) {
-                // Stream complete: every later tile's prefix is >= nitems.
-                if (threadIdx.x == 0)
-                    st_relaxed(ps.status + t, kFlagPrefix | (unsigned long long)ps.nitems);
-            } else if (((uintptr_t)out % (2 * sizeof(T))) == 0) {
-                ok = polar_tile<THREADS, BPT, MODE, T, true>(sm, out, ps, rk, t, bp.hdr, bp.spin_limit_ns);
-            } else {
-                ok = polar_tile<THREADS, BPT, MODE, T, false>(sm, out, ps, rk, t, bp.hdr, bp.spin_limit_ns);
+            const bool aligned = ((uintptr_t)out % (2 * sizeof(T))) == 0;
+            for (long long t = t0; t < t1; ++t) {
+                if (t > t0) {
+                    // overflow item: stop once the stream is complete
+                    if (threadIdx.x == 0) s_done = ld_relaxed_s32(ps.done);
+                    __syncthreads();
+                    skip = s_done;
+                    __syncthreads();
+                    if (skip) break;
+                }
+                if (skip) {
+                    // Stream complete: every later tile's prefix is >= nitems.
+                    if (threadIdx.x == 0) st_relaxed(ps.status + t, kFlagPrefix | (unsigned long long)ps.nitems);
+                } else if (aligned) {
+                    ok = polar_tile<THREADS, BPT, MODE, T, true>(sm, out, ps, rk, t, bp.hdr, bp.spin_limit_ns);
+                } else {
+                    ok = polar_tile<THREADS, BPT, MODE, T, false>(sm, out, ps, rk, t, bp.hdr, bp.spin_limit_ns);
+                }
+                __syncthreads();
+                if (!ok) break;
             }
         }
         __syncthreads();
@@ -277,19 +332,13 @@ template <int THREADS, int BPT, int MODE, typename T>
 static cudaError_t batched_main(const BatchedParams &bp, cudaStream_t s)
 {
     static int occ = 0;
-    const size_t dyn = (bp.k <= kSmemStreams) ? (size_t)(bp.k + 1) * sizeof(int) : 0;
     if (occ == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_batched<THREADS, BPT, MODE, T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)((kSmemStreams + 1) * sizeof(int)));
-        if (e != cudaSuccess) return e;
         int o = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batched<THREADS, BPT, MODE, T>, THREADS,
-                                                          (kSmemStreams + 1) * sizeof(int));
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batched<THREADS, BPT, MODE, T>, THREADS, 0);
         if (e != cudaSuccess) return e;
         occ = std::max(o, 1);
     }
-    k_batched<THREADS, BPT, MODE, T><<<sm_count() * occ, THREADS, dyn, s>>>(bp);
+    k_batched<THREADS, BPT, MODE, T><<<sm_count() * occ, THREADS, 0, s>>>(bp);
     return cudaGetLastError();
 }
 

@@ -340,6 +340,15 @@ __device__ __forceinline__ bool polar_tile(PolarSmem<THREADS, ROWS> &sm, T *__re
                                                                                         limit_ns, known_prefix);
 }
 
+// Next tile id of a single rejection stream, or -1 once the stream is
+// complete or the tile budget is spent.
+__device__ __forceinline__ long long claim_tile(const PolarParams &p)
+{
+    if (ld_relaxed_s32(&p.hdr->done) != 0) return -1;
+    const long long t = (long long)atomicAdd(&p.hdr->tile_counter, 1ull);
+    return t < p.tiles_max ? t : -1;
+}
+
 // One rejection stream over the whole grid: persistent CTAs take tile ids
 // from the workspace counter until the stream is complete (done) or the tile
 // budget is spent.
@@ -365,14 +374,7 @@ k_reject(const PolarParams p)
     T *out = static_cast<T *>(p.out);
 
     for (;;) {
-        if (threadIdx.x == 0) {
-            long long t = -1;
-            if (ld_relaxed_s32(&p.hdr->done) == 0) {
-                t = (long long)atomicAdd(&p.hdr->tile_counter, 1ull);
-                if (t >= p.tiles_max) t = -1;
-            }
-            s_tile = t;
-        }
+        if (threadIdx.x == 0) s_tile = claim_tile(p);
         __syncthreads();
         const long long t = s_tile;
         if (t < 0) break;

@@ -93,6 +93,32 @@ def test_batched_full_workload_sampled():
         assert_close(out[o:o + n], ref, mu, sg, "accurate", f"stream {j}")
 
 
+def test_batched_full_workload_every_short_stream():
+    """The same 4096-stream launch in every tile configuration; every stream
+    of at most 2e4 normals (about a third of them: one or two primary tiles,
+    the rest from the overflow item) checked whole."""
+    wl, desc, d_desc, out, ws = make_batch(W.BATCH_STREAMS, W.BATCH_LEN_LO, W.BATCH_LEN_HI, "mixed", align=4)
+    short = np.flatnonzero(wl.n <= 20000)
+    assert short.size > 1000
+    refs = {}
+    for j in short:
+        n, mu, sg, key = int(wl.n[j]), float(wl.mu[j]), float(wl.sigma[j]), int(wl.key[j])
+        refs[j] = oracle.boxmuller(n, mu, sg, key, 0) if wl.method[j] == 0 else oracle.polar(n, mu, sg, key, 0)[0]
+    for config in range(nr.nrng_batched_config_count()):
+        out.fill_(0.0)
+        nr.nrng_batched_set_config(torch.float32, "accurate", config)
+        try:
+            nr.nrng_batched(out, d_desc, len(desc), ws, "accurate")
+            assert nr.nrng_get_status(ws) == 0
+        finally:
+            nr.nrng_batched_set_config(torch.float32, "accurate", -1)
+        got = out.cpu()
+        for j in short:
+            o, n = int(wl.offset[j]), int(wl.n[j])
+            assert_close(got[o:o + n], refs[j], float(wl.mu[j]), float(wl.sigma[j]), "accurate",
+                         f"config {config} stream {j}")
+
+
 def test_batched_graph_and_autotune_agree():
     wl, desc, d_desc, out, ws = make_batch(96, 10, 50000, "mixed", align=1)
     nr.nrng_batched(out, d_desc, len(desc), ws, "fast")

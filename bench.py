@@ -267,24 +267,63 @@ class Step:
             if events is not None:
                 events[i][1].record()
 
+    E2E_COPY_STREAMS = 4
+
+    def _copy_out(self, host, dev, ready):
+        """Device -> pinned host copy of `dev`, split into one chunk per copy
+        stream, each stream waiting for `ready` (the producing part)."""
+        torch = self.torch
+        h, d = host.view(-1), dev.view(-1)
+        n = d.numel()
+        step = (n + len(self.copy_streams) - 1) // len(self.copy_streams)
+        for i, cs in enumerate(self.copy_streams):
+            lo, hi = i * step, min(n, (i + 1) * step)
+            if lo >= hi:
+                continue
+            cs.wait_event(ready)
+            with torch.cuda.stream(cs):
+                h[lo:hi].copy_(d[lo:hi], non_blocking=True)
+
     def run_e2e(self):
         """The step through host buffers: inputs in from pinned memory, every
-        output back to pinned memory."""
+        output back to pinned memory.  Each part's output is copied out on
+        separate copy streams while the next part computes; a part waits for
+        the previous step's copies of its own output before overwriting it,
+        and the step ends when every copy is done."""
         torch = self.torch
+        if not hasattr(self, "copy_streams"):
+            self.copy_streams = [torch.cuda.Stream() for _ in range(self.E2E_COPY_STREAMS)]
+            self.copied = {}
+        main = torch.cuda.current_stream()
+
+        def produce(name, outs, fn):
+            for e in self.copied.get(name, ()):
+                main.wait_event(e)   # the previous step's copies of these outputs
+            fn()
+            ready = torch.cuda.Event()
+            ready.record(main)
+            for host, dev in outs:
+                self._copy_out(host, dev, ready)
+            ev = []
+            for cs in self.copy_streams:
+                e = torch.cuda.Event()
+                e.record(cs)
+                ev.append(e)
+            self.copied[name] = ev
+
         self.mu.copy_(self.h_mu.view(self.rep_shape), non_blocking=True)
         self.sigma.copy_(self.h_sigma.view(self.rep_shape), non_blocking=True)
         self.w.copy_(self.h_w.view(self.rep_shape), non_blocking=True)
         self.desc_dev.copy_(self.h_desc, non_blocking=True)
-        self.part_b1()
-        self.h_b1.copy_(self.out_b1, non_blocking=True)
-        self.part_polar()
-        self.h_p.copy_(self.out_p, non_blocking=True)
-        self.part_batch()
-        self.h_batch.copy_(self.out_batch, non_blocking=True)
-        self.part_reparam()
-        self.h_x.copy_(self.x, non_blocking=True)
-        self.h_dmu.copy_(self.dmu, non_blocking=True)
-        self.h_dsigma.copy_(self.dsigma, non_blocking=True)
+        produce("b1", [(self.h_b1, self.out_b1)], self.part_b1)
+        produce("polar", [(self.h_p, self.out_p)], self.part_polar)
+        produce("batch", [(self.h_batch, self.out_batch)], self.part_batch)
+        produce("reparam", [(self.h_x, self.x), (self.h_dmu, self.dmu), (self.h_dsigma, self.dsigma)],
+                self.part_reparam)
+        for cs in self.copy_streams:   # the step ends when its copies are done
+            e = torch.cuda.Event()
+            e.record(cs)
+            main.wait_event(e)
 
     def e2e_bytes(self):
         h2d = 3 * self.n_rep * 4 + self.h_desc.numel()
@@ -363,40 +402,117 @@ def precision_sweep(step, K, W, peak):
     return out
 
 
-def cpu_oracle_sample(seconds_budget: float = 12.0):
-    """Times the FP64 oracle (single thread) on a bounded sample of the step's
-    mix: B1 and Polar at equal counts plus a slice of the batched streams and
-    of the reparameterised sample."""
+def write_ceiling(buf, K, W):
+    """What a plain write of the same 1 GiB achieves on this GPU: the
+    runtime's cudaMemsetAsync and torch's vectorised fill kernel (a plain
+    16-byte store loop), each the mean of K launches after W warm-ups."""
+    import torch
+    res = {"bytes": buf.numel() * buf.element_size()}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(W):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        return round(res["bytes"] / (ms * 1e-3) / 1e9, 1)
+
+    res["fill_GB_per_s"] = timed(lambda: buf.fill_(1.0))
+    try:
+        rt = ctypes.CDLL("libcudart.so.13")
+        rt.cudaMemsetAsync.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]
+        ptr, nbytes, hs = ctypes.c_void_p(buf.data_ptr()), ctypes.c_size_t(res["bytes"]), \
+            ctypes.c_void_p(stream.cuda_stream)
+
+        def memset():
+            if rt.cudaMemsetAsync(ptr, 0, nbytes, hs) != 0:
+                raise RuntimeError("cudaMemsetAsync failed")
+        res["memset_GB_per_s"] = timed(memset)
+    except (OSError, AttributeError, RuntimeError) as e:
+        res["memset_GB_per_s"] = None
+        res["memset_note"] = str(e)[:80]
+    return res
+
+
+def _oracle_work(task):
+    """One worker's share of the oracle sample (module level, so that a spawn
+    pool can run it): B1 and Polar of n normals each at this worker's own
+    counter, and optionally a slice of the batched streams and of the
+    reparameterised sample.  Returns the normals produced."""
     import oracle
     from paper_1004_3105_gb300 import workloads as W
+    n, counter, reps, extras = task
+    normals = 0
+    for _ in range(reps):
+        oracle.boxmuller(n, 0.0, 1.0, KEY, counter)
+        oracle.polar(n, 0.0, 1.0, KEY, counter)
+        normals += 2 * n
+        if extras:
+            wl = W.batched_workload(k=64, methods="mixed")
+            oracle.batched(wl.total, wl.as_dict())
+            rw = W.reparam_workload(shape=(64, 8192))
+            m = rw.mu.size
+            x = oracle.reparam_fwd(rw.mu, rw.sigma, m, 1, KEY + 1, counter)
+            oracle.reparam_bwd((2 * rw.w.ravel() * x).astype(np.float32), m, 1, KEY + 1, counter)
+            normals += wl.total + m
+    return normals
+
+
+class OraclePool:
+    """The oracle on every host core: a process pool started with spawn (the
+    process already holds a CUDA context, and a forked child of it can hang),
+    warmed up before any timing, one task per worker at disjoint counters."""
+
+    def __init__(self, workers=None):
+        import multiprocessing as mp
+        self.workers = workers or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.workers)
+        self.pool.map(_oracle_work, [(1 << 12, 0, 1, True)] * self.workers)   # import, build, load
+
+    def run(self, n, reps, extras):
+        tasks = [(n, w * (1 << 40), reps, extras) for w in range(self.workers)]
+        t0 = time.perf_counter()
+        normals = sum(self.pool.map(_oracle_work, tasks))
+        return normals, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_oracle_sample(seconds_budget: float = 12.0):
+    """Times the FP64 oracle on a bounded sample of the step's mix (B1 and
+    Polar at equal counts plus a slice of the batched streams and of the
+    reparameterised sample): on one core, and on every core of the host with
+    one worker process per core."""
+    import oracle
     oracle.build()
     n = 1 << 21
     t0 = time.perf_counter()
-    oracle.boxmuller(n, 0.0, 1.0, KEY, 0)
-    oracle.polar(n, 0.0, 1.0, KEY, 0)
-    wl = W.batched_workload(k=64, methods="mixed")
-    oracle.batched(wl.total, wl.as_dict())
-    rw = W.reparam_workload(shape=(64, 8192))
-    m = rw.mu.size
-    x = oracle.reparam_fwd(rw.mu, rw.sigma, m, 1, KEY + 1, 0)
-    oracle.reparam_bwd((2 * rw.w.ravel() * x).astype(np.float32), m, 1, KEY + 1, 0)
-    dt = time.perf_counter() - t0
-    normals = 2 * n + wl.total + m
-    scale = max(1, int(seconds_budget / max(dt, 1e-3)))
-    # repeat to fill the budget (bounded: at most ~seconds_budget of CPU work)
-    reps = min(scale, 8)
+    _oracle_work((n, 0, 1, True))
+    dt1 = time.perf_counter() - t0
+    reps = max(1, min(8, int(seconds_budget / 2 / max(dt1, 1e-3))))
     t0 = time.perf_counter()
-    for _ in range(reps):
-        oracle.boxmuller(n, 0.0, 1.0, KEY, 0)
-        oracle.polar(n, 0.0, 1.0, KEY, 0)
-        oracle.batched(wl.total, wl.as_dict())
-        x = oracle.reparam_fwd(rw.mu, rw.sigma, m, 1, KEY + 1, 0)
-        oracle.reparam_bwd((2 * rw.w.ravel() * x).astype(np.float32), m, 1, KEY + 1, 0)
-    dt = time.perf_counter() - t0
-    return {"value": reps * normals / dt, "unit": "normals/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} x (B1 2^21 + Polar 2^21 + 64 batched streams ({wl.total} normals) + "
-                      f"reparam fwd+bwd [64, 8192]), FP64 single-threaded C oracle",
-            "seconds": round(dt, 2)}
+    normals1 = _oracle_work((n, 0, reps, True))
+    dt1 = time.perf_counter() - t0
+    one = {"value": normals1 / dt1, "unit": "normals/s", "cores": 1, "seconds": round(dt1, 2)}
+    sample = (f"{reps} x (B1 2^21 + Polar 2^21 + 64 batched streams + reparam fwd+bwd [64, 8192]) per worker, "
+              f"FP64 C oracle, disjoint counters per worker")
+    try:
+        pool = OraclePool()
+        normals, dt = pool.run(n, reps, True)
+        pool.close()
+        return {"value": normals / dt, "unit": "normals/s", "cores": pool.workers, "kind": "oracle",
+                "sample": sample, "seconds": round(dt, 2), "single_core": one}
+    except Exception as e:   # no pool on this host: the single-core figure stands
+        log(f"oracle pool unavailable ({e}); single-core baseline only")
+        return {"value": one["value"], "unit": "normals/s", "cores": 1, "kind": "oracle", "sample": sample,
+                "seconds": one["seconds"]}
 
 
 # ------------------------------------------------------------------- arms --
@@ -407,27 +523,26 @@ def bench_reference(args):
     import oracle
     oracle.build()
     n = 1 << 20
-    t_list = []
-
-    def step():
-        oracle.boxmuller(n, 0.0, 1.0, KEY, 0)
-        oracle.polar(n, 0.0, 1.0, KEY, 0)
-
+    pool = OraclePool()
     for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
+        pool.run(n, 1, False)
+    total, dt = 0, 0.0
     for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    value = args.steps * 2 * n / dt
+        normals, t = pool.run(n, 1, False)
+        total += normals
+        dt += t
+    pool.close()
+    value = total / dt
+    per_step = total // max(1, args.steps)
     line = {
         "impl": "reference", "metric": "normals/s", "value": value, "unit": "normals/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "B1 + Polar normals, sample of 2^20 each per step (oracle), key 0x5EED0001",
-                   "sample_per_step": 2 * n},
-        "cpu_baseline": {"value": value, "unit": "normals/s", "cores": 1, "kind": "oracle",
-                         "sample": f"B1 2^20 + Polar 2^20 per step, {args.steps} steps"},
+        "config": {"workload": f"B1 + Polar normals, 2^20 each per worker per step on {pool.workers} host cores "
+                               f"(FP64 oracle), key 0x5EED0001",
+                   "sample_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": "normals/s", "cores": pool.workers, "kind": "oracle",
+                         "sample": f"B1 2^20 + Polar 2^20 per worker per step, {args.steps} steps"},
         "e2e": {"value": value, "unit": "normals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -520,8 +635,10 @@ def bench_ours(args):
     # alone with CUDA events (mean of K launches after W warm-ups), not part of
     # the step
     sweep = {}
+    ceiling = None
     if not args.no_sweep:
         sweep = precision_sweep(step, K, args.warmup, peak)
+        ceiling = write_ceiling(step.out_b1, K, args.warmup)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -537,7 +654,8 @@ def bench_ours(args):
                        "N": N_FULL, "batched_normals": step.batch_total, "reparam_shape": list(step.rep_shape),
                        "l2": "every output > L2 (1 GiB per single-stream kernel); no flush",
                        "parallelism": f"replicas x{world}"},
-            "parts": parts, "sweep": sweep, "roofline": roofline, "clocks": clocks.summary(),
+            "parts": parts, "sweep": sweep, "write_ceiling": ceiling, "roofline": roofline,
+            "clocks": clocks.summary(),
             "e2e": e2e, "gpu_launches": K * step.our_launches_per_step, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -86,3 +86,20 @@ def z_bins(ref: np.ndarray, got: np.ndarray, mu: float, sigma: float):
         else:
             rows.append((lo, hi, 0, 0.0, 0.0, 0.0))
     return rows
+
+
+def record_error_table(what: str, gpu: torch.Tensor, ref: np.ndarray, mu: float, sigma: float, n_total: int):
+    """Appends the |z|-binned error rows of one variant to the JSON-lines file
+    named by NRNG_ERROR_TABLE, when that variable is set (the precision-sweep
+    error table); a no-op otherwise."""
+    import json
+    import os
+    path = os.environ.get("NRNG_ERROR_TABLE")
+    if not path:
+        return
+    got = gpu.detach().float().cpu().numpy().astype(np.float64)
+    rows = z_bins(ref, got, mu, sigma)
+    with open(path, "a") as f:
+        f.write(json.dumps({"variant": what, "sampled": int(got.size), "of": int(n_total), "mu": mu,
+                            "sigma": sigma, "bins": rows}) + "\n")
+

@@ -10,7 +10,7 @@ import torch
 
 import oracle
 import paper_1004_3105_gb300 as nr
-from gpu_helpers import assert_close, sync
+from gpu_helpers import assert_close, record_error_table, sync
 from paper_1004_3105_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -76,4 +76,6 @@ def test_precision_sweep_sampled(method, mode, dtype, polar_full):
         pairs = W.sample_indices(N // 2, 1 << 17)
         ref = oracle.polar_at(cand[pairs], mu, sigma, W.KEY_MAIN, 0).ravel()
         idx = np.stack([2 * pairs, 2 * pairs + 1], axis=1).ravel()
-    assert_close(out[torch.from_numpy(idx).cuda()], ref, mu, sigma, mode, f"sweep {method} {mode} {dtype}")
+    got = out[torch.from_numpy(idx).cuda()]
+    assert_close(got, ref, mu, sigma, mode, f"sweep {method} {mode} {dtype}")
+    record_error_table(f"{method} {mode} {str(dtype).replace('torch.', '')}", got, ref, mu, sigma, N)

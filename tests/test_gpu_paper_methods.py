@@ -11,7 +11,7 @@ import torch
 
 import oracle
 import paper_1004_3105_gb300 as nr
-from gpu_helpers import assert_canary, assert_close, canary_tensor, sync
+from gpu_helpers import assert_canary, assert_close, canary_tensor, record_error_table, sync
 from paper_1004_3105_gb300 import workloads as W
 from stats import check_standard_normal_moments, ks_critical, ks_distance, normal_cdf
 
@@ -183,3 +183,35 @@ def test_ratio_normality(mode):
     z = out.cpu().numpy().astype(np.float64)
     check_standard_normal_moments(z)
     assert ks_distance(z, normal_cdf) < ks_critical(n)
+
+
+@pytest.mark.parametrize("method", ["b2", "b3", "p2", "ratio_accurate", "ratio_fast"])
+def test_paper_methods_sweep_parameters(method):
+    """N = 2^24 at the precision sweep's mu 1.5, sigma 0.25, fp32: sampled
+    outputs against the oracle (and the |z|-binned error table when
+    NRNG_ERROR_TABLE is set)."""
+    n, mu, sigma = 1 << 24, W.SWEEP_MU, W.SWEEP_SIGMA
+    out = torch.empty(n, device="cuda")
+    idx = W.sample_indices(n, 1 << 17)
+    tol = "fast"
+    if method == "b2":
+        nr.nrng_boxmuller(out, mu, sigma, W.KEY_MAIN, 0, mode="b2")
+        ref = oracle.boxmuller_at(idx, mu, sigma, W.KEY_MAIN, 0)
+    elif method == "b3":
+        nr.nrng_boxmuller_b3(out, mu, sigma, W.KEY_MAIN, 0)
+        groups = np.unique(idx // 8)
+        idx = (8 * groups[:, None] + np.arange(8)).ravel()
+        ref = np.concatenate([oracle.b3(8, mu, sigma, W.KEY_MAIN, 3 * int(g)) for g in groups])
+    elif method == "p2":
+        out, _, _ = run_p2(n, mu, sigma, W.KEY_MAIN, 0)
+        ref = oracle.polar_p2(n, mu, sigma, W.KEY_MAIN, 0)[0][idx]
+    else:
+        mode = method.split("_")[1]
+        out, cand, _ = run_ratio(n, mu, sigma, W.KEY_MAIN, 0, mode)
+        ref = oracle.ratio_at(cand[idx], mu, sigma, W.KEY_MAIN, 0)
+        tol = mode
+    sync()
+    got = out[torch.from_numpy(idx).cuda()]
+    assert_close(got, ref, mu, sigma, tol, f"{method} 2^24")
+    record_error_table(f"{method} f32", got, ref, mu, sigma, n)
+

@@ -35,7 +35,7 @@ static cudaError_t polar_launch_t(const PolarParams &p, bool aligned, cudaStream
 {
     static int occ_aligned = 0, occ_plain = 0;
     int &occ = aligned ? occ_aligned : occ_plain;
-    auto kern = aligned ? k_reject<PolarPolicy<MODE>, MODE, T, true> : k_reject<PolarPolicy<MODE>, MODE, T, false>;
+    auto kern = aligned ? k_reject<PolarPolicy<MODE>, 1536, T, true> : k_reject<PolarPolicy<MODE>, 1536, T, false>;
     if (occ == 0) {
         int o = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kPolarThreads, 0);

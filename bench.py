@@ -185,6 +185,34 @@ class ClockSampler:
                 "reasons": sorted(self.reasons), "samples": len(self.samples), "source": "nvml"}
 
 
+def bind_to_gpu_cpus(cuda_index: int):
+    """Restricts this process to the host CPUs NVML reports as closest to the
+    GPU (read only: a process setting, nothing on the GPU changes), so that
+    the pinned host buffers of the end-to-end step are first touched in the
+    GPU's local memory.  Returns the CPU list applied, or None."""
+    try:
+        import torch
+        nvml = ctypes.CDLL("libnvidia-ml.so.1")
+        if nvml.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(cuda_index).uuid)
+        if nvml.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) != 0:
+            return None
+        words = 64
+        mask = (ctypes.c_ulong * words)()
+        if nvml.nvmlDeviceGetCpuAffinity(h, words, mask) != 0:
+            return None
+        cpus = {64 * i + b for i in range(words) for b in range(64) if (mask[i] >> b) & 1}
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return sorted(cpus)
+    except (OSError, AttributeError, RuntimeError):
+        return None
+
+
 # ------------------------------------------------------------ GPU workload --
 class Step:
     """Buffers and launches of one step of the hot path on one GPU."""
@@ -558,6 +586,8 @@ def bench_ours(args):
     torch.cuda.set_device(local)
     import paper_1004_3105_gb300 as nr
     nr.load()
+    cpus_all = os.sched_getaffinity(0)
+    cpus_gpu = bind_to_gpu_cpus(local) if not args.no_e2e else None
     step = Step(rank, host_io=not args.no_e2e)
     torch.cuda.synchronize()
 
@@ -605,7 +635,8 @@ def bench_ours(args):
         h2d, d2h = step.e2e_bytes()
         e2e = {"value": world * Ke * step.normals_per_step / (ems * 1e-3), "unit": "normals/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": Ke,
-               "ms_per_step": ems / Ke}
+               "ms_per_step": ems / Ke, "d2h_GB_per_s": round(d2h / (ems / Ke * 1e-3) / 1e9, 1),
+               "host_cpus": (f"{len(cpus_gpu)} GPU-local cpus" if cpus_gpu else "unbound")}
 
     # ---- roofline of the dominant kernel and per-part rates
     peak, peak_src = measured_peaks()
@@ -641,6 +672,7 @@ def bench_ours(args):
         ceiling = write_ceiling(step.out_b1, K, args.warmup)
 
     cpu = None
+    os.sched_setaffinity(0, cpus_all)   # the CPU baseline uses every core
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(args.cpu_seconds)
 

@@ -41,6 +41,12 @@ int batched_config_count() { return kNumConfigs; }
 BatchedConfig batched_config(int id) { return kConfigs[id]; }
 int batched_default_config() { return 1; }
 
+// B1 tiles per B1 work item: a claim (an atomic and three dependent loads
+// while the CTA waits) is amortised over two tiles.  Measured on the
+// 4096-stream workload: 2 is 3.5% faster than 1 on all-B1 batches; 4 loses
+// on mixed batches to the longer tail of the last items.
+constexpr int kB1TilesPerItem = 2;
+
 __host__ __device__ inline int64_t b1_items(int64_t n, int64_t tile_blocks)
 {
     const int64_t nblocks = (n + 3) / 4;
@@ -80,7 +86,7 @@ __host__ __device__ inline void stream_items(const nrng_stream_desc_t &d, int th
     if (d.n == 0) return;
     const int64_t tile_blocks = (int64_t)threads * bpt;
     if (d.method == NRNG_B1) {
-        items = b1_items(d.n, tile_blocks);
+        items = b1_items(d.n, tile_blocks * kB1TilesPerItem);
         const uint64_t blocks = (uint64_t)((d.n + 3) / 4);
         if (d.counter > ULLONG_MAX - (blocks - 1)) items = -2;
     } else {
@@ -284,10 +290,15 @@ k_batched(BatchedParams bp)
         if (d.method == NRNG_B1) {
             if (overflow) {
                 // B1 streams have no overflow tiles
-            } else if (((uintptr_t)out % (4 * sizeof(T))) == 0)
-                b1_tile<THREADS, BPT, MODE, T, true>(out, d.n, d.mu, d.sigma, rk, d.counter, t0);
-            else
-                b1_tile<THREADS, BPT, MODE, T, false>(out, d.n, d.mu, d.sigma, rk, d.counter, t0);
+            } else if (((uintptr_t)out % (4 * sizeof(T))) == 0) {
+                for (int q = 0; q < kB1TilesPerItem; ++q)
+                    b1_tile<THREADS, BPT, MODE, T, true>(out, d.n, d.mu, d.sigma, rk, d.counter,
+                                                         t0 * kB1TilesPerItem + q);
+            } else {
+                for (int q = 0; q < kB1TilesPerItem; ++q)
+                    b1_tile<THREADS, BPT, MODE, T, false>(out, d.n, d.mu, d.sigma, rk, d.counter,
+                                                          t0 * kB1TilesPerItem + q);
+            }
         } else if (!(overflow && skip)) {
             PolarStream ps;
             ps.n = d.n;

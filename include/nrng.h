@@ -64,9 +64,12 @@ typedef enum {
 
 typedef enum { NRNG_F32 = 0, NRNG_BF16 = 1, NRNG_F16 = 2 } nrng_dtype_t;
 
-/* NRNG_ACCURATE: CUDA's correctly rounded or 1-ulp functions (log1pf and
- *   sincospif for B1; logf of s held as an exact double-float, reciprocal and
- *   sqrtf for P).  Error within 4e-6 max(1, |z|) of the FP64 definition.
+/* NRNG_ACCURATE: the logarithms and the sine and cosine by CUDA's library
+ *   functions (log1pf and sincospif for B1; logf of s held as an exact
+ *   double-float for P); square roots and P's reciprocal by the hardware
+ *   approximations, whose relative error (below 2^-22) moves a result by
+ *   under 2e-7 of itself.  Error within 4e-6 max(1, |z|) of the FP64
+ *   definition.
  * NRNG_FAST: the hardware approximations (log2, sqrt, rsqrt, sin, cos) with a
  *   short series for ln(1 - d) at small d, where the approximate log loses
  *   relative accuracy.  Error within 2e-5 max(1, |z|).

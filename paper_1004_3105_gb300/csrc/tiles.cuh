@@ -52,7 +52,7 @@ struct PolarSmem {
     static constexpr int kEntries = ROWS * kWarps;   // (row, warp) segments
     static constexpr int kSeg = 64 * ROWS;           // most accepted points a warp holds
     int2 seg[kWarps][kSeg];      // each warp's accepted points in candidate order; step-4 results in place
-    uint16_t cl[kWarps][kSeg];   // local candidate index of each entry
+    uint2 mask[kEntries];        // (row, warp) accept ballots of the two candidate halves
     int off[kEntries];           // (row, warp) counts, then exclusive offsets
     int total;                   // accepted points of the tile
     long long prefix;
@@ -125,6 +125,27 @@ __device__ __forceinline__ void store_item_bits(T *p, int2 v)
 }
 
 // ------------------------------------------------------------ policies ----
+// Local candidate index (within the tile) of the j-th accepted candidate of
+// row r, warp w, from the row's accept ballots m = (half 0, half 1): the
+// candidates of a row run lane by lane, half 0 before half 1.  Only the
+// careful copy-out (candidate indices requested, or the stream's last tile)
+// needs it, so a binary search over the lanes replaces a stored index per
+// accepted point.
+template <int THREADS>
+__device__ __forceinline__ int accepted_candidate(uint2 m, int j, int r, int w)
+{
+    int L = 0;   // the lane holding item j: most accepted points below it <= j
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const unsigned lt = (1u << (L + step)) - 1u;
+        if (__popc(m.x & lt) + __popc(m.y & lt) <= j) L += step;
+    }
+    const unsigned lt = (1u << L) - 1u;
+    const int before = __popc(m.x & lt) + __popc(m.y & lt);
+    const int h = (((m.x >> L) & 1u) && before == j) ? 0 : 1;
+    return 2 * (r * THREADS + w * 32 + L) + h;
+}
+
 // A rejection method on the candidate stream: each candidate is the two words
 // 2h, 2h+1 of a Philox block (h = 0, 1); accept() decides it and keeps a
 // payload, transform() turns an accepted payload into kOut output values.
@@ -199,7 +220,6 @@ __device__ __forceinline__ bool reject_tile(PolarSmem<THREADS, ROWS> &sm, T *__r
     const bool silent = (t == ps.silent_tile);
     const unsigned lt = (1u << lane) - 1u;
     int2 *seg = sm.seg[warp];
-    uint16_t *cl = sm.cl[warp];
 
     // A: steps 1-3, compacted per warp.
     int rowbase[ROWS + 1];   // warp-uniform: start of each row's run in the segment
@@ -214,17 +234,13 @@ __device__ __forceinline__ bool reject_tile(PolarSmem<THREADS, ROWS> &sm, T *__r
         const unsigned m0 = __ballot_sync(0xFFFFFFFFu, a0);
         const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1);
         const int pos = base + __popc(m0 & lt) + __popc(m1 & lt);
-        const uint16_t c = (uint16_t)(2 * (r * THREADS + tid));
-        if (a0) {
-            seg[pos] = p0;
-            cl[pos] = c;
-        }
-        if (a1) {
-            seg[pos + (a0 ? 1 : 0)] = p1;
-            cl[pos + (a0 ? 1 : 0)] = (uint16_t)(c + 1);
-        }
+        if (a0) seg[pos] = p0;
+        if (a1) seg[pos + (a0 ? 1 : 0)] = p1;
         const int cnt = __popc(m0) + __popc(m1);
-        if (lane == 0) sm.off[r * kWarps + warp] = cnt;
+        if (lane == 0) {
+            sm.off[r * kWarps + warp] = cnt;
+            sm.mask[r * kWarps + warp] = make_uint2(m0, m1);
+        }
         rowbase[r] = base;
         base += cnt;
     }
@@ -321,7 +337,7 @@ __device__ __forceinline__ bool reject_tile(PolarSmem<THREADS, ROWS> &sm, T *__r
                 if (gl < lim_full) memcpy(&tile_out[2 * gl + 1], &hi, 2);
             }
             if (ps.pair_cand || gl == lim - 1) {
-                const long long c = t * kCand + cl[rowbase[r] + j];
+                const long long c = t * kCand + accepted_candidate<THREADS>(sm.mask[r * kWarps + warp], j, r, warp);
                 if (ps.pair_cand) ps.pair_cand[P + gl] = c;
                 if (P + gl == ps.nitems - 1) {
                     if (ps.next_counter) *ps.next_counter = ps.counter + (uint64_t)(c / 2) + 1u;

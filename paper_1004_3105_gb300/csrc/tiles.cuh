@@ -14,22 +14,39 @@ __device__ __forceinline__ void b1_tile(T *__restrict__ out, int64_t n, float mu
                                         const Key &rk, uint64_t counter, int64_t t)
 {
     const int64_t nblocks = (n + 3) / 4;
-#pragma unroll 2
-    for (int r = 0; r < BPT; ++r) {
+    // Two rows per step when both are in range: the two Philox chains are
+    // independent and fill each other's multiply stalls.
+    for (int r = 0; r < BPT; r += 2) {
         const int64_t b = t * (THREADS * BPT) + r * THREADS + threadIdx.x;
-        if (b >= nblocks) break;
-        const uint4 w = philox_block(counter + (uint64_t)b, rk);
-        float x0, y0, x1, y1;
-        b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
-        b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
-        const int64_t i = 4 * b;
-        if (ALIGNED && i + 4 <= n) {
-            store4_aligned(out + i, x0, y0, x1, y1);
-        } else {
-            if (i < n) store1(out + i, x0);
-            if (i + 1 < n) store1(out + i + 1, y0);
-            if (i + 2 < n) store1(out + i + 2, x1);
-            if (i + 3 < n) store1(out + i + 3, y1);
+        const int64_t b2 = b + THREADS;
+        if (b2 < nblocks && ALIGNED && 4 * b2 + 4 <= n) {
+            const uint4 w = philox_block(counter + (uint64_t)b, rk);
+            const uint4 w2 = philox_block(counter + (uint64_t)b2, rk);
+            float x0, y0, x1, y1, x2, y2, x3, y3;
+            b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
+            b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
+            b1_pair<MODE>(w2.x, w2.y, mu, sigma, x2, y2);
+            b1_pair<MODE>(w2.z, w2.w, mu, sigma, x3, y3);
+            store4_aligned(out + 4 * b, x0, y0, x1, y1);
+            store4_aligned(out + 4 * b2, x2, y2, x3, y3);
+            continue;
+        }
+        for (int q = 0; q < 2; ++q) {
+            const int64_t bq = b + q * THREADS;
+            if (bq >= nblocks) return;
+            const uint4 w = philox_block(counter + (uint64_t)bq, rk);
+            float x0, y0, x1, y1;
+            b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
+            b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
+            const int64_t i = 4 * bq;
+            if (ALIGNED && i + 4 <= n) {
+                store4_aligned(out + i, x0, y0, x1, y1);
+            } else {
+                if (i < n) store1(out + i, x0);
+                if (i + 1 < n) store1(out + i + 1, y0);
+                if (i + 2 < n) store1(out + i + 2, x1);
+                if (i + 3 < n) store1(out + i + 3, y1);
+            }
         }
     }
 }

@@ -287,7 +287,7 @@ __device__ __forceinline__ bool reject_tile(PolarSmem<THREADS, ROWS> &sm, T *__r
     }
 
     // C: the transform over this warp's segment, dense, results in place.
-#pragma unroll 1
+#pragma unroll 2
     for (int j = lane; j < base; j += 32) {
         float za, zb;
         Policy::transform(seg[j], ps.mu, ps.sigma, za, zb);
@@ -320,10 +320,14 @@ __device__ __forceinline__ bool reject_tile(PolarSmem<THREADS, ROWS> &sm, T *__r
         for (int r = 0; r < ROWS; ++r) {
             const int o = sm.off[r * kWarps + warp];
             const int rb = rowbase[r];
-            const int cnt = rowbase[r + 1] - rb;
-            for (int j = lane; j < cnt; j += 32) {
-                if (K == 2) store_pair_bits<T>(tile_out + 2 * (o + j), seg[rb + j], true);
-                else store_item_bits<T>(tile_out + (o + j), seg[rb + j]);
+            const int cnt = rowbase[r + 1] - rb;   // at most 64: two steps of 32 lanes
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = lane + 32 * h;
+                if (j < cnt) {
+                    if (K == 2) store_pair_bits<T>(tile_out + 2 * (o + j), seg[rb + j], true);
+                    else store_item_bits<T>(tile_out + (o + j), seg[rb + j]);
+                }
             }
         }
         return true;

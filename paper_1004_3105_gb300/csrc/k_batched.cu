@@ -219,11 +219,14 @@ struct BatchedWork {
 __device__ __forceinline__ void batched_claim(const BatchedParams &bp, unsigned long long total_items,
                                               unsigned long long primary, int cand, int &last, BatchedWork &w)
 {
-    long long item = -1;
-    if (ld_relaxed_s32(&bp.hdr->done) == 0) {
-        const unsigned long long it = atomicAdd(&bp.hdr->tile_counter, 1ull);
-        if (it < total_items) item = (long long)it;
-    }
+    // The error flag and the claim are issued together (one round trip, not
+    // two); an item claimed after an error is dropped unprocessed.  This flag
+    // is set only on an error, and every look-back gives up as soon as the
+    // status word is set, so a dropped item never holds up a successor.
+    // (Stream completion is the per-stream flag, read after the claim.)
+    const int failed = ld_relaxed_s32(&bp.hdr->done);
+    const unsigned long long it = atomicAdd(&bp.hdr->tile_counter, 1ull);
+    const long long item = (failed == 0 && it < total_items) ? (long long)it : -1;
     if (item < 0) {
         w.stream = -1;
         return;
@@ -254,10 +257,13 @@ __device__ __forceinline__ void batched_claim(const BatchedParams &bp, unsigned 
         w.t0 = bp.item_prefix[j + 1] - bp.item_prefix[j];   // the stream's primary tiles
         w.overflow = 1;
     }
+    // The descriptor and the stream's completion flag are loaded together
+    // (B1 streams' flags stay 0).
+    const int stream_done = ld_relaxed_s32(bp.stream_done + j);
     w.d = bp.desc[j];
     const bool polar = (w.d.method == NRNG_POLAR);
     if (w.overflow) w.t1 = polar ? polar_tiles_for(w.d.n, cand) : w.t0;   // B1 has no overflow
-    w.skip = polar ? ld_relaxed_s32(bp.stream_done + j) : 0;
+    w.skip = polar ? stream_done : 0;
     w.stream = j;
 }
 

@@ -382,6 +382,10 @@ __device__ __forceinline__ bool polar_tile(PolarSmem<THREADS, ROWS> &sm, T *__re
 
 // Next tile id of a single rejection stream, or -1 once the stream is
 // complete or the tile budget is spent.
+// The completion flag is read before the claim, never alongside it: a tile
+// claimed and then dropped would never publish, and a later tile's look-back
+// would wait on it until its limit.  (Issuing the two together was measured:
+// an occasional call ran into that wait.)
 __device__ __forceinline__ long long claim_tile(const PolarParams &p)
 {
     if (ld_relaxed_s32(&p.hdr->done) != 0) return -1;

@@ -215,3 +215,22 @@ def test_paper_methods_sweep_parameters(method):
     assert_close(got, ref, mu, sigma, tol, f"{method} 2^24")
     record_error_table(f"{method} f32", got, ref, mu, sigma, n)
 
+
+@pytest.mark.parametrize("method", ["polar", "p2", "ratio"])
+def test_repeated_calls_status_clean(method):
+    """Back-to-back calls on one workspace, the status read after every call:
+    a tile claimed after the stream completed must never hold up a later
+    tile's look-back (which would surface here as NRNG_ERR_TIMEOUT)."""
+    n = 1 << 24
+    out = torch.empty(n, device="cuda")
+    ws = nr.ratio_workspace(n) if method == "ratio" else nr.polar_workspace(n)
+    for c in range(40):
+        if method == "polar":
+            nr.nrng_polar(out, 0.0, 1.0, W.KEY_MAIN, c, ws, "fast")
+        elif method == "p2":
+            nr.nrng_polar_p2(out, 0.0, 1.0, W.KEY_MAIN, c, ws)
+        else:
+            nr.nrng_ratio(out, 0.0, 1.0, W.KEY_MAIN, c, ws, "fast")
+        status = nr.nrng_get_status(ws)
+        assert status == 0, (c, nr._lib.STATUS[status])
+

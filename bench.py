@@ -366,6 +366,15 @@ class Step:
                 raise RuntimeError(f"device status {nr._lib.STATUS.get(st, st)}")
 
 
+def check_ws(nr, ws):
+    """Raises if the workspace's device status word reports an error.  Each
+    call clears its workspace first, so the warm-up calls are checked one by
+    one: an error in a timed loop would be hidden by the next call."""
+    st = nr.nrng_get_status(ws)
+    if st != 0:
+        raise RuntimeError(f"device status {nr._lib.STATUS.get(st, st)}")
+
+
 def precision_sweep(step, K, W, peak):
     """{B1, Polar} x {accurate, fast} x {f32, bf16, f16} at N = 2^28, then
     Methods B2, B3, P2, R and the two-pass Polar in f32."""
@@ -385,6 +394,8 @@ def precision_sweep(step, K, W, peak):
                         nr.nrng_polar(buf, 1.5, 0.25, KEY, step.base, step.ws_p, mode)
                 for _ in range(W):
                     run()
+                    if method == "polar":
+                        check_ws(nr, step.ws_p)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 for _ in range(K):
@@ -409,9 +420,13 @@ def precision_sweep(step, K, W, peak):
         "polar_twopass_accurate_f32": lambda: nr.nrng_polar_twopass(buf, 1.5, 0.25, KEY, step.base, ws_2, "accurate"),
         "polar_twopass_fast_f32": lambda: nr.nrng_polar_twopass(buf, 1.5, 0.25, KEY, step.base, ws_2, "fast"),
     }
+    checked_ws = {"p2_f32": step.ws_p, "ratio_accurate_f32": ws_r, "ratio_fast_f32": ws_r,
+                  "polar_twopass_accurate_f32": ws_2, "polar_twopass_fast_f32": ws_2}
     for name, run in variants.items():
         for _ in range(W):
             run()
+            if name in checked_ws:
+                check_ws(nr, checked_ws[name])
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(K):
@@ -594,8 +609,8 @@ def bench_ours(args):
     # ---- device-resident timed region
     for _ in range(args.warmup):
         step.run_parts()
+        step.check_status()   # per warm-up step: the next step's clear would hide an error
     torch.cuda.synchronize()
-    step.check_status()
     K = args.steps
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in Step.PARTS] for _ in range(K)]

@@ -242,7 +242,8 @@ class Step:
         self.rep_shape = W.REPARAM_SHAPE
         self.mu = torch.from_numpy(rw.mu).to(dev)
         self.sigma = torch.from_numpy(rw.sigma).to(dev)
-        self.w = torch.from_numpy(rw.w).to(dev)
+        # the loss sum(w x^2) has gradient 2 w x: keep 2w so that it is one multiply
+        self.w2 = torch.from_numpy(2.0 * rw.w).to(dev)
         self.x = torch.empty(self.rep_shape, dtype=torch.float32, device=dev)
         self.g = torch.empty_like(self.x)
         self.dmu = torch.empty_like(self.mu)
@@ -263,7 +264,7 @@ class Step:
             self.h_dsigma = torch.empty(self.rep_shape, **pin)
             self.h_mu = torch.from_numpy(rw.mu).pin_memory()
             self.h_sigma = torch.from_numpy(rw.sigma).pin_memory()
-            self.h_w = torch.from_numpy(rw.w).pin_memory()
+            self.h_w2 = torch.from_numpy(2.0 * rw.w).pin_memory()
             self.h_desc = torch.from_numpy(desc.view(np.uint8).copy()).pin_memory()
         self.normals_per_step = 2 * N_FULL + self.batch_total + self.n_rep
         # our kernels per step: B1 1, Polar 1, batched 2 (prep + main), reparam fwd + bwd 2
@@ -281,8 +282,7 @@ class Step:
     def part_reparam(self):
         nr = self.nr
         nr.nrng_reparam_fwd(self.x, self.mu, self.sigma, KEY + 1, self.base, "accurate")
-        self.torch.mul(self.w, self.x, out=self.g)
-        self.g.mul_(2.0)
+        self.torch.mul(self.w2, self.x, out=self.g)   # dL/dx = 2 w x
         nr.nrng_reparam_bwd(self.dmu, self.dsigma, self.g, KEY + 1, self.base, "accurate")
 
     PARTS = ("b1", "polar", "batch", "reparam")
@@ -341,7 +341,7 @@ class Step:
 
         self.mu.copy_(self.h_mu.view(self.rep_shape), non_blocking=True)
         self.sigma.copy_(self.h_sigma.view(self.rep_shape), non_blocking=True)
-        self.w.copy_(self.h_w.view(self.rep_shape), non_blocking=True)
+        self.w2.copy_(self.h_w2.view(self.rep_shape), non_blocking=True)
         self.desc_dev.copy_(self.h_desc, non_blocking=True)
         produce("b1", [(self.h_b1, self.out_b1)], self.part_b1)
         produce("polar", [(self.h_p, self.out_p)], self.part_polar)

@@ -86,11 +86,22 @@ def measured_peaks():
         return PEAK_FALLBACK_GBS, "fallback"
 
 
-def source_digest() -> str:
-    """Digest of the kernel sources, to tell whether recorded counters are stale."""
+# The sources each recorded kernel is compiled from (its translation unit and
+# the headers it includes).
+KERNEL_SOURCES = {
+    "k_b1": ["k_b1.cu", "nrng_device.cuh", "nrng_internal.h", "h_poly.inc"],
+    "k_polar": ["k_polar.cu", "tiles.cuh", "nrng_device.cuh", "nrng_internal.h", "h_poly.inc"],
+    "k_batched": ["k_batched.cu", "tiles.cuh", "nrng_device.cuh", "nrng_internal.h", "h_poly.inc"],
+}
+
+
+def source_digest(kernel: str = None) -> str:
+    """Digest of a kernel's sources (of all kernel sources when kernel is
+    None), to tell whether recorded counters are stale."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1004_3105_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    names = KERNEL_SOURCES.get(kernel) if kernel else None
+    for name in sorted(names or os.listdir(csrc)):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -105,7 +116,7 @@ def recorded_traffic(kernel: str):
         with open(p) as f:
             d = json.load(f)
         rec = d.get(kernel)
-        if rec and rec.get("source_digest") == source_digest():
+        if rec and rec.get("source_digest") == source_digest(kernel):
             return float(rec["dram_bytes_per_launch"])
     except Exception:
         pass

@@ -214,6 +214,21 @@ int32_t nrng_ratio(void *d_out, int64_t n, float mu, float sigma, uint64_t key,
                    uint64_t counter, int32_t dtype, int32_t mode, void *d_ws, size_t ws_bytes,
                    uint64_t *d_next_counter, int64_t *d_candidate, nrng_stream_t stream);
 
+/* Diagnostics (no counterpart in the paper): the per-pair transforms at
+ * caller-given inputs, so that tests reach lattice points a stream reaches
+ * too rarely (s -> 1, S = 1, u = 0, u = 1 - 2^-24, the quadrant angles).
+ * kind 0 (NRNG_B1): d_in holds n pairs of 32-bit Philox words (wu, wv);
+ *   d_out[2i], d_out[2i + 1] receive B1's x, y for that pair, exactly as
+ *   nrng_boxmuller computes them (mode NRNG_ACCURATE, NRNG_FAST or NRNG_B2).
+ * kind 1 (NRNG_POLAR): d_in holds n pairs of int32 lattice coordinates
+ *   (kx', ky') in [-2^23, 2^23); d_accept[i] (nullable) receives Algorithm P's
+ *   step-3 decision (1 iff 0 < S < 2^46) and d_out[2i], d_out[2i + 1] step 4's
+ *   values as nrng_polar computes them, meaningful only where accepted
+ *   (mode NRNG_ACCURATE or NRNG_FAST).
+ * d_in: 2n x 4 bytes, 4-byte aligned; d_out: 2n floats; d_accept: n int32. */
+int32_t nrng_eval_points(int32_t kind, int32_t mode, const void *d_in, int64_t n, float mu, float sigma,
+                         float *d_out, int32_t *d_accept, nrng_stream_t stream);
+
 /* Polar without a workspace, for callers that cannot allocate device memory
  * (no counterpart in the paper).  Some callers cannot obtain the workspace
  * nrng_polar needs: code running inside a host application that owns the
@@ -288,7 +303,8 @@ int32_t nrng_batched_config_count(void);
 int32_t nrng_batched_config_info(int32_t config, int32_t *h_threads, int32_t *h_blocks_per_thread);
 
 /* Pins the configuration nrng_batched uses for (dtype, mode); -1 restores
- * the default.  Thread-safe. */
+ * the default (the built-in one, or configuration NRNG_FORCE_CONFIG=<id> from
+ * the environment when set to a valid id).  Thread-safe. */
 int32_t nrng_batched_set_config(int32_t dtype, int32_t mode, int32_t config);
 int32_t nrng_batched_get_config(int32_t dtype, int32_t mode, int32_t *h_config);
 

@@ -9,7 +9,7 @@ from .nrng import (  # noqa: F401
     ACCURATE, B1, B2, FAST, POLAR, STREAM_DESC, BatchedGraph, Reparam, broadcast_layout, descriptors_to_device,
     nrng_batched, nrng_batched_autotune, nrng_batched_config_count, nrng_batched_config_info,
     nrng_batched_get_config, nrng_batched_set_config, nrng_batched_workspace_size, nrng_boxmuller,
-    nrng_boxmuller_b3, nrng_get_status, nrng_polar, nrng_polar_max_blocks, nrng_polar_noalloc, nrng_polar_p2,
+    nrng_boxmuller_b3, nrng_eval_points, nrng_get_status, nrng_polar, nrng_polar_max_blocks, nrng_polar_noalloc, nrng_polar_p2,
     nrng_polar_twopass, nrng_polar_twopass_workspace_size, nrng_polar_workspace_size, nrng_ratio,
     nrng_ratio_workspace_size, nrng_reparam_bwd, nrng_reparam_fwd, nrng_uniform, polar_workspace,
     raise_on_status, ratio_workspace, stream_descriptors,

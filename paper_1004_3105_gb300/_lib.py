@@ -53,6 +53,7 @@ SIGNATURES = {
     "nrng_polar_p2": (_I32, [_P, _I64, _F32, _F32, _U64, _U64, _I32, _P, _SZ, _P, _P, _P]),
     "nrng_ratio_workspace_size": (_I32, [_I64, _PSZ]),
     "nrng_ratio": (_I32, [_P, _I64, _F32, _F32, _U64, _U64, _I32, _I32, _P, _SZ, _P, _P, _P]),
+    "nrng_eval_points": (_I32, [_I32, _I32, _P, _I64, _F32, _F32, _P, _P, _P]),
     "nrng_batched_workspace_size": (_I32, [_P, _I32, _PSZ]),
     "nrng_batched": (_I32, [_P, _P, _I32, _I32, _I32, _P, _SZ, _P]),
     "nrng_reparam_fwd": (_I32, [_P, _P, _P, _I64, _I64, _I64, _U64, _U64, _I32, _P]),

@@ -11,9 +11,20 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nrng_internal.h"
 
 namespace nrng {
+
+// An NVTX range around each entry point that enqueues GPU work, so that a
+// timeline tool shows every call by name (a no-op without a tool attached).
+struct CallRange {
+    explicit CallRange(const char *name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange &) = delete;
+    CallRange &operator=(const CallRange &) = delete;
+};
 
 // ------------------------------------------------------------- helpers ----
 static int log_level()
@@ -106,11 +117,27 @@ static bool counter_fits(uint64_t counter, uint64_t blocks)
 static std::mutex g_cfg_mutex;
 static int g_cfg[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
 
+// NRNG_FORCE_CONFIG=<id> replaces the built-in default configuration (a
+// configuration pinned with nrng_batched_set_config still wins); an id out
+// of range is ignored.
+static int env_default_config()
+{
+    static int v = [] {
+        const char *e = std::getenv("NRNG_FORCE_CONFIG");
+        if (e == nullptr || *e < '0' || *e > '9') return -1;   // unset, empty or not a number
+        const int c = std::atoi(e);
+        return c < batched_config_count() ? c : -1;
+    }();
+    return v;
+}
+
 static int batched_config_for(int32_t dtype, int32_t mode)
 {
     std::lock_guard<std::mutex> lock(g_cfg_mutex);
     const int c = g_cfg[dtype][mode];
-    return c >= 0 ? c : batched_default_config();
+    if (c >= 0) return c;
+    const int forced = env_default_config();
+    return forced >= 0 ? forced : batched_default_config();
 }
 
 }  // namespace nrng
@@ -139,6 +166,7 @@ int32_t nrng_abi_version(void) { return 1; }
 
 int32_t nrng_uniform(float *d_out, int64_t n, uint64_t key, uint64_t counter, nrng_stream_t stream)
 {
+    const CallRange range("nrng_uniform");
     if (n < 0 || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if ((uintptr_t)d_out % 4) return NRNG_ERR_MISALIGNED;
     if (n == 0) return NRNG_OK;
@@ -149,6 +177,7 @@ int32_t nrng_uniform(float *d_out, int64_t n, uint64_t key, uint64_t counter, nr
 int32_t nrng_boxmuller(void *d_out, int64_t n, float mu, float sigma, uint64_t key, uint64_t counter,
                        int32_t dtype, int32_t mode, nrng_stream_t stream)
 {
+    const CallRange range("nrng_boxmuller");
     if (n < 0 || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if (!valid_dtype(dtype) || !(valid_mode(mode) || mode == NRNG_B2)) return NRNG_ERR_INVALID_VALUE;
     if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
@@ -178,6 +207,7 @@ int32_t nrng_polar(void *d_out, int64_t n, float mu, float sigma, uint64_t key, 
                    int32_t dtype, int32_t mode, void *d_ws, size_t ws_bytes, uint64_t *d_next_counter,
                    int64_t *d_pair_candidate, nrng_stream_t stream)
 {
+    const CallRange range("nrng_polar");
     if (n < 0 || n > kPolarMaxN || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if (!valid_dtype(dtype) || !valid_mode(mode)) return NRNG_ERR_INVALID_VALUE;
     if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
@@ -224,6 +254,7 @@ int32_t nrng_polar_twopass(void *d_out, int64_t n, float mu, float sigma, uint64
                            int32_t dtype, int32_t mode, void *d_ws, size_t ws_bytes, uint64_t *d_next_counter,
                            int64_t *d_pair_candidate, nrng_stream_t stream)
 {
+    const CallRange range("nrng_polar_twopass");
     if (n < 0 || n > kPolarMaxN || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if (!valid_dtype(dtype) || !valid_mode(mode)) return NRNG_ERR_INVALID_VALUE;
     if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
@@ -261,6 +292,7 @@ int32_t nrng_polar_twopass(void *d_out, int64_t n, float mu, float sigma, uint64
 int32_t nrng_boxmuller_b3(void *d_out, int64_t n, float mu, float sigma, uint64_t key, uint64_t counter,
                           int32_t dtype, nrng_stream_t stream)
 {
+    const CallRange range("nrng_boxmuller_b3");
     if (n < 0 || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if (!valid_dtype(dtype)) return NRNG_ERR_INVALID_VALUE;
     if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
@@ -305,6 +337,7 @@ int32_t nrng_polar_p2(void *d_out, int64_t n, float mu, float sigma, uint64_t ke
                       int32_t dtype, void *d_ws, size_t ws_bytes, uint64_t *d_next_counter,
                       int64_t *d_pair_candidate, nrng_stream_t stream)
 {
+    const CallRange range("nrng_polar_p2");
     if (n < 0 || n > kPolarMaxN || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if (!valid_dtype(dtype)) return NRNG_ERR_INVALID_VALUE;
     if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
@@ -334,6 +367,7 @@ int32_t nrng_ratio(void *d_out, int64_t n, float mu, float sigma, uint64_t key, 
                    int32_t mode, void *d_ws, size_t ws_bytes, uint64_t *d_next_counter, int64_t *d_candidate,
                    nrng_stream_t stream)
 {
+    const CallRange range("nrng_ratio");
     if (n < 0 || n > kPolarMaxN || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if (!valid_dtype(dtype) || !valid_mode(mode)) return NRNG_ERR_INVALID_VALUE;
     if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
@@ -349,6 +383,21 @@ int32_t nrng_ratio(void *d_out, int64_t n, float mu, float sigma, uint64_t key, 
     if (st != NRNG_OK) return st;
     const bool aligned = ((uintptr_t)d_out % (2 * dtype_size(dtype))) == 0;
     return cuda_status(launch_ratio(p, dtype, mode, aligned, (cudaStream_t)stream), "nrng_ratio");
+}
+
+int32_t nrng_eval_points(int32_t kind, int32_t mode, const void *d_in, int64_t n, float mu, float sigma,
+                         float *d_out, int32_t *d_accept, nrng_stream_t stream)
+{
+    const CallRange range("nrng_eval_points");
+    if (kind != NRNG_B1 && kind != NRNG_POLAR) return NRNG_ERR_INVALID_VALUE;
+    if (!(valid_mode(mode) || (mode == NRNG_B2 && kind == NRNG_B1))) return NRNG_ERR_INVALID_VALUE;
+    if (n < 0 || (n > 0 && (d_in == nullptr || d_out == nullptr))) return NRNG_ERR_INVALID_VALUE;
+    if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
+    if ((uintptr_t)d_in % 4 || (uintptr_t)d_out % 4 || (uintptr_t)d_accept % 4) return NRNG_ERR_MISALIGNED;
+    if (n == 0) return NRNG_OK;
+    return cuda_status(launch_eval_points(kind, mode, static_cast<const uint32_t *>(d_in), n, mu, sigma, d_out,
+                                          d_accept, (cudaStream_t)stream),
+                       "nrng_eval_points");
 }
 
 int32_t nrng_batched_workspace_size(const nrng_stream_desc_t *h_desc, int32_t k, size_t *h_bytes)
@@ -372,6 +421,7 @@ static int32_t batched_check(void *d_out, const nrng_stream_desc_t *d_desc, int3
 int32_t nrng_batched(void *d_out, const nrng_stream_desc_t *d_desc, int32_t k, int32_t dtype, int32_t mode,
                      void *d_ws, size_t ws_bytes, nrng_stream_t stream)
 {
+    const CallRange range("nrng_batched");
     const int32_t st = batched_check(d_out, d_desc, k, dtype, mode, d_ws, ws_bytes);
     if (st != NRNG_OK || k == 0) return st;
     return cuda_status(launch_batched(d_out, d_desc, k, dtype, mode, d_ws, ws_bytes,
@@ -382,6 +432,7 @@ int32_t nrng_batched(void *d_out, const nrng_stream_desc_t *d_desc, int32_t k, i
 int32_t nrng_reparam_fwd(float *d_x, const float *d_mu, const float *d_sigma, int64_t n, int64_t m,
                          int64_t inner, uint64_t key, uint64_t counter, int32_t mode, nrng_stream_t stream)
 {
+    const CallRange range("nrng_reparam_fwd");
     if (n < 0 || m < 1 || inner < 1 || !valid_mode(mode)) return NRNG_ERR_INVALID_VALUE;
     if (n > 0 && (d_x == nullptr || d_mu == nullptr || d_sigma == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if (m > INT64_MAX / inner || n % (m * inner) != 0) return NRNG_ERR_INVALID_VALUE;
@@ -395,6 +446,7 @@ int32_t nrng_reparam_fwd(float *d_x, const float *d_mu, const float *d_sigma, in
 int32_t nrng_reparam_bwd(float *d_dmu, float *d_dsigma, const float *d_g, int64_t n, int64_t m, int64_t inner,
                          uint64_t key, uint64_t counter, int32_t mode, nrng_stream_t stream)
 {
+    const CallRange range("nrng_reparam_bwd");
     if (n < 0 || m < 1 || inner < 1 || !valid_mode(mode)) return NRNG_ERR_INVALID_VALUE;
     if (n > 0 && (d_dsigma == nullptr || d_g == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if (m > INT64_MAX / inner || n % (m * inner) != 0) return NRNG_ERR_INVALID_VALUE;
@@ -407,6 +459,7 @@ int32_t nrng_reparam_bwd(float *d_dmu, float *d_dsigma, const float *d_g, int64_
 
 int32_t nrng_get_status(const void *d_ws, nrng_stream_t stream, int32_t *h_status)
 {
+    const CallRange range("nrng_get_status");
     if (d_ws == nullptr || h_status == nullptr) return NRNG_ERR_INVALID_VALUE;
     int32_t v = 0;
     cudaError_t e = cudaMemcpyAsync(&v, d_ws, sizeof(v), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
@@ -449,6 +502,7 @@ int32_t nrng_batched_autotune(void *d_out, const nrng_stream_desc_t *d_desc, int
                               int32_t mode, void *d_ws, size_t ws_bytes, int32_t reps, nrng_stream_t stream,
                               int32_t *h_config, float *h_ms)
 {
+    const CallRange range("nrng_batched_autotune");
     int32_t st = batched_check(d_out, d_desc, k, dtype, mode, d_ws, ws_bytes);
     if (st != NRNG_OK) return st;
     if (k == 0 || reps < 1) return NRNG_ERR_INVALID_VALUE;
@@ -506,6 +560,7 @@ int32_t nrng_batched_graph_create(void *d_out, const nrng_stream_desc_t *d_desc,
                                   int32_t mode, void *d_ws, size_t ws_bytes, nrng_stream_t stream,
                                   void **h_graph)
 {
+    const CallRange range("nrng_batched_graph_create");
     if (h_graph == nullptr || stream == nullptr) return NRNG_ERR_INVALID_VALUE;
     int32_t st = batched_check(d_out, d_desc, k, dtype, mode, d_ws, ws_bytes);
     if (st != NRNG_OK) return st;
@@ -533,6 +588,7 @@ int32_t nrng_batched_graph_create(void *d_out, const nrng_stream_desc_t *d_desc,
 
 int32_t nrng_graph_launch(void *h_graph, nrng_stream_t stream)
 {
+    const CallRange range("nrng_graph_launch");
     if (h_graph == nullptr) return NRNG_ERR_INVALID_VALUE;
     return cuda_status(cudaGraphLaunch(static_cast<NrngGraph *>(h_graph)->exec, (cudaStream_t)stream),
                        "graph launch");

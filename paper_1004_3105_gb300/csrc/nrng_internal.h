@@ -113,6 +113,8 @@ cudaError_t launch_polar_twopass(const PolarParams &p, int dtype, int mode, bool
 // The paper's further methods (Sec. 3-5): B3, P2 and the Ratio method R.
 cudaError_t launch_b3(void *out, int64_t n, float mu, float sigma, uint64_t key, uint64_t counter, int dtype,
                       bool aligned, cudaStream_t s);
+cudaError_t launch_eval_points(int kind, int mode, const uint32_t *in, int64_t n, float mu, float sigma,
+                               float *out, int32_t *accept, cudaStream_t s);
 cudaError_t launch_polar_p2(const PolarParams &p, int dtype, bool aligned, cudaStream_t s);
 cudaError_t launch_ratio(const PolarParams &p, int dtype, int mode, bool aligned, cudaStream_t s);
 int64_t ratio_tiles_max(int64_t n);

@@ -197,6 +197,24 @@ def nrng_ratio(out: torch.Tensor, mu: float, sigma: float, key: int, counter: in
           "nrng_ratio")
 
 
+def nrng_eval_points(kind: int, points: torch.Tensor, mu: float = 0.0, sigma: float = 1.0, mode="accurate",
+                     stream=None):
+    """The per-pair transform at given inputs (diagnostics).  kind B1: points
+    is an [n, 2] uint32/int32 tensor of Philox words (wu, wv); kind POLAR: an
+    [n, 2] int32 tensor of lattice coordinates (kx', ky').  Returns (values
+    [n, 2] float32, accept [n] int32)."""
+    if points.dim() != 2 or points.shape[1] != 2 or points.element_size() != 4:
+        raise ValueError("points must be an [n, 2] tensor of 32-bit words")
+    pts = points.contiguous()
+    n = pts.shape[0]
+    out = torch.empty((n, 2), dtype=torch.float32, device=pts.device)
+    acc = torch.empty(n, dtype=torch.int32, device=pts.device)
+    check(load().nrng_eval_points(int(kind), _mode(mode), _dev(pts, "points"), n, float(mu), float(sigma),
+                                  _dev(out, "out"), _dev(acc, "accept"), _stream(stream)),
+          "nrng_eval_points")
+    return out, acc
+
+
 def nrng_polar_noalloc(out: torch.Tensor, mu: float, sigma: float, key: int, counter: int, mode="accurate",
                        next_counter: torch.Tensor = None, pair_candidate: torch.Tensor = None,
                        status: torch.Tensor = None, stream=None) -> None:

@@ -206,3 +206,44 @@ def test_config_table(lib):
     assert lib.nrng_batched_set_config(0, 1, -1) == _lib.OK
     assert lib.nrng_batched_get_config(0, 1, ctypes.byref(c)) == _lib.OK and c.value == 1
     assert lib.nrng_batched_set_config(0, 1, 99) == _lib.ERR_INVALID_VALUE
+
+
+def test_eval_points_validation(lib):
+    f = lib.nrng_eval_points
+    assert f(7, 0, FAKE, 4, 0.0, 1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE      # kind
+    assert f(1, 2, FAKE, 4, 0.0, 1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE      # B2 is a B1 mode
+    assert f(0, 5, FAKE, 4, 0.0, 1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE
+    assert f(0, 0, None, 4, 0.0, 1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE
+    assert f(0, 0, FAKE, 4, 0.0, -1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE
+    assert f(0, 0, ODD, 4, 0.0, 1.0, FAKE, None, None) == _lib.ERR_MISALIGNED
+    assert f(1, 0, FAKE, 4, 0.0, 1.0, FAKE, ODD, None) == _lib.ERR_MISALIGNED
+    assert f(0, 0, None, 0, 0.0, 1.0, None, None, None) == _lib.OK
+
+
+def test_launch_failure_maps_to_err_cuda(lib):
+    """With no usable GPU a launch fails inside the runtime: the call returns
+    NRNG_ERR_CUDA instead of crashing.  (Runs only where there is no GPU: with
+    one, the fake output pointer would be written.)"""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    assert lib.nrng_uniform(FAKE, 8, 1, 0, None) == _lib.ERR_CUDA
+    assert lib.nrng_boxmuller(FAKE, 8, 0.0, 1.0, 1, 0, 0, 0, None) == _lib.ERR_CUDA
+
+
+def test_force_config_env():
+    """NRNG_FORCE_CONFIG replaces the default batched configuration (read once
+    per process, so checked in a child)."""
+    import subprocess
+    import sys
+    code = ("import ctypes; from paper_1004_3105_gb300 import _lib; lib = _lib.load(); c = ctypes.c_int32(-9); "
+            "assert lib.nrng_batched_get_config(0, 0, ctypes.byref(c)) == 0; print(c.value)")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for env_val, want in (("4", 4), ("99", None), ("", None)):
+        env = dict(os.environ, NRNG_FORCE_CONFIG=env_val)
+        out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                             timeout=300)
+        assert out.returncode == 0, out.stderr
+        got = int(out.stdout.strip())
+        assert got == (want if want is not None else 1), (env_val, got)
+

@@ -1,0 +1,91 @@
+"""The per-pair transforms at hand-picked lattice points, through
+nrng_eval_points, against the oracle: the special points of Algorithm B1
+(u = 0, u = 1 - 2^-24, v on the quadrant angles) and of Algorithm P
+(S = 1, S = 2, S just below and at 2^46, s -> 1, the origin), which a stream
+reaches too rarely to test.  Accept decisions bit-exact; values within the
+mode's tolerance."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1004_3105_gb300 as nr
+from gpu_helpers import assert_close
+
+pytestmark = pytest.mark.gpu
+MU, SIGMA = 0.75, 1.25
+
+
+def b1_words():
+    rng = np.random.Generator(np.random.PCG64(5))
+    ks = [0, 1, 2, 255, 1 << 12, (1 << 23) - 1, 1 << 23, (1 << 24) - 2, (1 << 24) - 1]
+    js = [0, 1, 1 << 22, (1 << 22) + 1, 1 << 23, (1 << 23) - 1, 3 << 22, (1 << 24) - 1]
+    k = np.array([a for a in ks for _ in js], dtype=np.uint64)
+    j = np.array([b for _ in ks for b in js], dtype=np.uint64)
+    # random low bytes: the lattice uses only the top 24 bits of each word
+    low = rng.integers(0, 256, size=(k.size, 2), dtype=np.uint64)
+    wu = (k << np.uint64(8)) | low[:, 0]
+    wv = (j << np.uint64(8)) | low[:, 1]
+    rnd = rng.integers(0, 1 << 32, size=(4096, 2), dtype=np.uint64)
+    w = np.concatenate([np.stack([wu, wv], axis=1), rnd]).astype(np.uint32)
+    return w
+
+
+@pytest.mark.parametrize("mode", ["accurate", "fast", "b2"])
+def test_b1_special_points(mode):
+    w = b1_words()
+    got, acc = nr.nrng_eval_points(nr.B1, torch.from_numpy(w.view(np.int32)).cuda(), MU, SIGMA, mode)
+    u = (w[:, 0] >> 8).astype(np.float64) * 2.0 ** -24
+    v = (w[:, 1] >> 8).astype(np.float64) * 2.0 ** -24
+    ref = oracle.b1_points(u, v, MU, SIGMA)
+    assert bool((acc == 1).all())
+    assert_close(got.reshape(-1), ref.reshape(-1), MU, SIGMA, "accurate" if mode == "accurate" else "fast",
+                 f"B1 points {mode}")
+    # u = 0 gives r = 0: both outputs are exactly mu
+    z = got.cpu().numpy()[(w[:, 0] >> 8) == 0]
+    assert np.all(z == np.float32(MU))
+
+
+def polar_points():
+    m = 1 << 23
+    pts = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, -1), (3, 4),
+           (m - 1, 0), (0, m - 1), (-(m - 1), 0), (-m, 0), (0, -m), (-m, 1), (-m, -m),
+           (m - 1, 1 << 11), (m - 1, (1 << 11) + 1), (m - 2, 4096), (5792, 5792)]
+    rng = np.random.Generator(np.random.PCG64(6))
+    # points just inside and just outside the unit circle (s -> 1)
+    th = rng.uniform(0.0, 2.0 * np.pi, 2048)
+    for eps in (0.0, 1e-7, 2e-6, -1e-7):
+        r = (m - 1) * (1.0 - eps)
+        pts += list(zip(np.clip(np.rint(r * np.cos(th)), -m, m - 1).astype(int),
+                        np.clip(np.rint(r * np.sin(th)), -m, m - 1).astype(int)))
+    # near the origin (s -> 0, the largest |z|) and uniform points
+    pts += list(zip(rng.integers(-64, 65, 1024), rng.integers(-64, 65, 1024)))
+    pts += list(zip(rng.integers(-m, m, 4096), rng.integers(-m, m, 4096)))
+    return np.array(pts, dtype=np.int32)
+
+
+@pytest.mark.parametrize("mode", ["accurate", "fast"])
+def test_polar_special_points(mode):
+    p = polar_points()
+    got, acc = nr.nrng_eval_points(nr.POLAR, torch.from_numpy(p).cuda(), MU, SIGMA, mode)
+    want = oracle.polar_accept_points(p[:, 0], p[:, 1])
+    acc = acc.cpu().numpy()
+    assert np.array_equal(acc, want.astype(np.int32)), "accept decisions"
+    # the boundary cases decide as Algorithm P's step 3 says
+    S = p[:, 0].astype(np.int64) ** 2 + p[:, 1].astype(np.int64) ** 2
+    assert np.array_equal(acc, ((S > 0) & (S < (1 << 46))).astype(np.int32))
+    assert acc[0] == 0 and acc[11] == 0 and acc[13] == 0          # origin, S = 2^46, S > 2^46
+    keep = np.flatnonzero(acc == 1)
+    ref = oracle.polar_points(p[keep, 0], p[keep, 1], MU, SIGMA)
+    assert_close(got[torch.from_numpy(keep).cuda()].reshape(-1), ref.reshape(-1), MU, SIGMA, mode,
+                 f"Polar points {mode}")
+
+
+def test_eval_points_validation():
+    pts = torch.zeros((4, 2), dtype=torch.int32, device="cuda")
+    with pytest.raises(nr.NrngError):
+        nr.nrng_eval_points(7, pts)
+    with pytest.raises(nr.NrngError):
+        nr.nrng_eval_points(nr.POLAR, pts, mode="b2")
+    out, acc = nr.nrng_eval_points(nr.POLAR, pts[:0])
+    assert out.shape == (0, 2) and acc.shape == (0,)

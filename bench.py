@@ -95,16 +95,25 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and whitespace: what the compiler sees."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return "".join(text.split())
+
+
 def source_digest(kernel: str = None) -> str:
     """Digest of a kernel's sources (of all kernel sources when kernel is
-    None), to tell whether recorded counters are stale."""
+    None), comments and whitespace left out, to tell whether recorded
+    counters are stale."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1004_3105_gb300", "csrc")
     names = KERNEL_SOURCES.get(kernel) if kernel else None
     for name in sorted(names or os.listdir(csrc)):
-        with open(os.path.join(csrc, name), "rb") as f:
+        with open(os.path.join(csrc, name), encoding="utf-8", errors="replace") as f:
             h.update(name.encode())
-            h.update(f.read())
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -30,8 +30,8 @@ namespace nrng {
 
 // ------------------------------------------------------------ configs -----
 // (threads per CTA, Philox blocks per thread per tile).  A Polar tile stages
-// at most 64 accepted points per warp and row, 10 bytes each, in shared
-// memory: 40 KB for 256 x 8.
+// at most 64 accepted points per warp and row, 8 bytes each, in shared
+// memory, plus 8 bytes of accept ballots per (row, warp): 33.6 KB for 256 x 8.
 static const BatchedConfig kConfigs[] = {
     {256, 4}, {256, 8}, {128, 8}, {512, 4}, {128, 4}, {512, 2},
 };

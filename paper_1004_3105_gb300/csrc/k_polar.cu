@@ -4,8 +4,8 @@
 // The paper vectorises P by generating vectors of (x, y, s), compressing out
 // the rejected triples and buffering the variable-length result (Sec. 2's
 // vector gather; Sec. 4, RANN3B/RANN3).  Here the compress is a decoupled
-// look-back scan over tiles of kPolarCandPerTile candidates (polar_tile in
-// tiles.cuh): a persistent CTA takes the next tile id from a global counter
+// look-back scan over tiles of kPolarCandPerTile candidates (k_reject and
+// reject_tile in tiles.cuh, with Algorithm P's policy): a persistent CTA takes the next tile id from a global counter
 // (dynamic ids, so a tile only ever waits on tiles already owned by running
 // CTAs); each warp draws its candidates, tests 0 < kx'^2 + ky'^2 < 2^46
 // exactly in 64-bit integers, compacts the accepted ones into its own

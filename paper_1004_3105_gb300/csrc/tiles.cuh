@@ -53,9 +53,7 @@ __device__ __forceinline__ void b1_tile(T *__restrict__ out, int64_t n, float mu
 
 // Resident threads per SM the Polar tile kernels are compiled for (sets the
 // register budget through __launch_bounds__: 40 registers a thread, without
-// spills).  Shared memory holds the single-stream kernel at 5 CTAs (1280
-// threads) per SM all the same; the tighter budget was measured 2.7% faster
-// than 48 registers at that occupancy.
+// spills).  With the 33.6 KB tile, six 256-thread CTAs fit per SM.
 template <int THREADS, int MODE>
 struct PolarOccupancy {
     static constexpr int kThreads = 1536;

@@ -130,8 +130,29 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
     const int32_t per = (bp.k + kPrepThreads - 1) / kPrepThreads;
     const int32_t j0 = tid * per;
     const int32_t j1 = (j0 + per < bp.k) ? j0 + per : bp.k;
+    // Each descriptor's items and slots are computed once (64-bit divisions
+    // and a square root) and kept for the second pass when they fit here.
+    constexpr int kKeep = 4;
+    int64_t keep_items[kKeep], keep_slots[kKeep];
     long long mi = 0, ms = 0;
-    for (int32_t j = j0; j < j1; ++j) {
+#pragma unroll
+    for (int q = 0; q < kKeep; ++q) {   // unrolled: the kept values stay in registers
+        keep_items[q] = keep_slots[q] = 0;
+        const int32_t j = j0 + q;
+        if (j >= j1) continue;
+        int64_t items, slots;
+        stream_items(bp.desc[j], threads, bpt, items, slots);
+        if (items < 0) {
+            atomicMax(&s_bad, items == -2 ? kStatusOverflow : kStatusInvalid);
+            items = 0;
+            slots = 0;
+        }
+        keep_items[q] = items;
+        keep_slots[q] = slots;
+        mi += items;
+        ms += slots;
+    }
+    for (int32_t j = j0 + kKeep; j < j1; ++j) {   // more than 4 descriptors a thread
         int64_t items, slots;
         stream_items(bp.desc[j], threads, bpt, items, slots);
         if (items < 0) {
@@ -165,7 +186,16 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
     }
     __syncthreads();
     long long ci = s_wi[warp] + ii - mi, cs = s_ws[warp] + is - ms;   // exclusive for this thread
-    for (int32_t j = j0; j < j1; ++j) {
+#pragma unroll
+    for (int q = 0; q < kKeep; ++q) {
+        const int32_t j = j0 + q;
+        if (j >= j1) continue;
+        bp.item_prefix[j] = ci;
+        bp.slot_base[j] = cs;
+        ci += keep_items[q];
+        cs += keep_slots[q];
+    }
+    for (int32_t j = j0 + kKeep; j < j1; ++j) {
         int64_t items, slots;
         stream_items(bp.desc[j], threads, bpt, items, slots);
         if (items < 0) { items = 0; slots = 0; }

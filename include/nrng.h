@@ -313,7 +313,10 @@ int32_t nrng_batched_get_config(int32_t dtype, int32_t mode, int32_t *h_config);
  * with its time in milliseconds per launch.  The workspace must be sized for
  * the largest tile count of any configuration (nrng_batched_workspace_size
  * already is).  If the environment variable NRNG_AUTOTUNE_CACHE names a file,
- * the choice is appended to it as one JSON line.  Synchronises `stream`. */
+ * it is a cache of earlier choices, one JSON line each, keyed by dtype, mode,
+ * the number of streams and a fingerprint of every stream's length and method:
+ * a matching line is used without timing anything (its time is returned),
+ * and a new choice is appended.  Synchronises `stream`. */
 int32_t nrng_batched_autotune(void *d_out, const nrng_stream_desc_t *d_desc, int32_t k,
                               int32_t dtype, int32_t mode, void *d_ws, size_t ws_bytes,
                               int32_t reps, nrng_stream_t stream, int32_t *h_config,

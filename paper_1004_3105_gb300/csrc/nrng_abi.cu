@@ -140,6 +140,62 @@ static int batched_config_for(int32_t dtype, int32_t mode)
     return forced >= 0 ? forced : batched_default_config();
 }
 
+// ---------------------------------------------------------- autotune cache
+// One JSON line per tuned workload in the file named by NRNG_AUTOTUNE_CACHE.
+// The fingerprint covers what the timing depends on: every stream's length
+// and method (not its key, counter, mu or sigma).
+static uint64_t workload_fingerprint(const nrng_stream_desc_t *h, int32_t k)
+{
+    uint64_t x = 1469598103934665603ull;   // FNV-1a, 64-bit
+    auto mix = [&x](uint64_t v) {
+        for (int b = 0; b < 8; ++b) {
+            x ^= (v >> (8 * b)) & 0xFFu;
+            x *= 1099511628211ull;
+        }
+    };
+    for (int32_t j = 0; j < k; ++j) {
+        mix((uint64_t)h[j].n);
+        mix((uint64_t)(uint32_t)h[j].method);
+    }
+    return x;
+}
+
+static const char *kCacheLine =
+    "{\"kernel\": \"batched\", \"dtype\": %d, \"mode\": %d, \"streams\": %d, \"fingerprint\": \"%016llx\", "
+    "\"config\": %d, \"threads\": %d, \"blocks_per_thread\": %d, \"ms\": %f}";
+
+static bool cache_lookup(const char *path, int32_t dtype, int32_t mode, int32_t k, uint64_t fp, int &cfg, float &ms)
+{
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        int d = -1, m = -1, kk = -1, c = -1, th = 0, bpt = 0;
+        unsigned long long g = 0;
+        float t = 0.0f;
+        if (std::sscanf(line, kCacheLine, &d, &m, &kk, &g, &c, &th, &bpt, &t) == 8 && d == dtype && m == mode &&
+            kk == k && g == fp && c >= 0 && c < batched_config_count()) {
+            cfg = c;   // the last matching line wins
+            ms = t;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+static void cache_store(const char *path, int32_t dtype, int32_t mode, int32_t k, uint64_t fp, int cfg, float ms)
+{
+    if (FILE *f = std::fopen(path, "a")) {
+        const BatchedConfig c = batched_config(cfg);
+        std::fprintf(f, kCacheLine, dtype, mode, k, (unsigned long long)fp, cfg, c.threads, c.blocks_per_thread,
+                     (double)ms);
+        std::fputc('\n', f);
+        std::fclose(f);
+    }
+}
+
 }  // namespace nrng
 
 using namespace nrng;
@@ -507,6 +563,28 @@ int32_t nrng_batched_autotune(void *d_out, const nrng_stream_desc_t *d_desc, int
     if (st != NRNG_OK) return st;
     if (k == 0 || reps < 1) return NRNG_ERR_INVALID_VALUE;
     cudaStream_t s = (cudaStream_t)stream;
+
+    // A cached choice for the same workload shape is reused without timing.
+    const char *cache = std::getenv("NRNG_AUTOTUNE_CACHE");
+    uint64_t fp = 0;
+    if (cache) {
+        std::vector<nrng_stream_desc_t> h((size_t)k);
+        if (cudaMemcpyAsync(h.data(), d_desc, sizeof(nrng_stream_desc_t) * (size_t)k, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return NRNG_ERR_CUDA;
+        fp = workload_fingerprint(h.data(), k);
+        int cfg = -1;
+        float ms = 0.0f;
+        if (cache_lookup(cache, dtype, mode, k, fp, cfg, ms)) {
+            nrng_batched_set_config(dtype, mode, cfg);
+            if (h_config) *h_config = cfg;
+            if (h_ms) *h_ms = ms;
+            log_msg("autotune: cached config %d for %d streams (%016llx)", cfg, k, (unsigned long long)fp);
+            return NRNG_OK;
+        }
+    }
+
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return NRNG_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return NRNG_ERR_CUDA; }
@@ -522,10 +600,11 @@ int32_t nrng_batched_autotune(void *d_out, const nrng_stream_desc_t *d_desc, int
         if (st != NRNG_OK) break;
         if (dev_status != NRNG_OK) { st = dev_status; break; }
         cudaEventRecord(e0, s);
-        for (int r = 0; r < reps; ++r)
-            launch_batched(d_out, d_desc, k, dtype, mode, d_ws, ws_bytes, c, s);
+        for (int r = 0; r < reps && st == NRNG_OK; ++r)
+            st = cuda_status(launch_batched(d_out, d_desc, k, dtype, mode, d_ws, ws_bytes, c, s), "autotune");
         cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { st = NRNG_ERR_CUDA; break; }
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = NRNG_ERR_CUDA;
+        if (st != NRNG_OK) break;
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         ms /= (float)reps;
@@ -539,15 +618,7 @@ int32_t nrng_batched_autotune(void *d_out, const nrng_stream_desc_t *d_desc, int
     nrng_batched_set_config(dtype, mode, best);
     if (h_config) *h_config = best;
     if (h_ms) *h_ms = best_ms;
-    if (const char *path = std::getenv("NRNG_AUTOTUNE_CACHE")) {
-        if (FILE *f = std::fopen(path, "a")) {
-            const BatchedConfig c = batched_config(best);
-            std::fprintf(f, "{\"kernel\": \"batched\", \"dtype\": %d, \"mode\": %d, \"streams\": %d, "
-                            "\"config\": %d, \"threads\": %d, \"blocks_per_thread\": %d, \"ms\": %.6f}\n",
-                         dtype, mode, k, best, c.threads, c.blocks_per_thread, best_ms);
-            std::fclose(f);
-        }
-    }
+    if (cache) cache_store(cache, dtype, mode, k, fp, best, best_ms);
     return NRNG_OK;
 }
 

@@ -142,6 +142,33 @@ def test_batched_graph_and_autotune_agree():
     assert torch.equal(out[:wl.total], direct[:wl.total])
 
 
+def test_batched_autotune_cache(tmp_path, monkeypatch):
+    """NRNG_AUTOTUNE_CACHE: the first tuning of a workload appends one line;
+    the same workload shape (other keys and parameters) reuses it without
+    timing; a different shape is tuned and appended."""
+    cache = tmp_path / "autotune.jsonl"
+    monkeypatch.setenv("NRNG_AUTOTUNE_CACHE", str(cache))
+    wl, desc, d_desc, out, ws = make_batch(40, 10, 20000, "mixed", align=1)
+    cfg, ms = nr.nrng_batched_autotune(out, d_desc, len(desc), ws, "accurate", reps=1)
+    assert len(cache.read_text().splitlines()) == 1
+    nr.nrng_batched_set_config(torch.float32, "accurate", -1)
+    desc2 = desc.copy()
+    desc2["key"] += 1000
+    desc2["mu"] = 0.5
+    cfg2, ms2 = nr.nrng_batched_autotune(out, nr.descriptors_to_device(desc2), len(desc2), ws, "accurate", reps=1)
+    assert cfg2 == cfg and ms2 == pytest.approx(ms, abs=2e-6)
+    assert len(cache.read_text().splitlines()) == 1
+    assert nr.nrng_batched_get_config(torch.float32, "accurate") == cfg
+    desc3 = desc.copy()
+    desc3["n"][0] += 1
+    desc3["offset"] = np.concatenate([[0], np.cumsum(desc3["n"])[:-1]])
+    ws3 = torch.empty(max(nr.nrng_batched_workspace_size(desc3), 256), dtype=torch.uint8, device="cuda")
+    out3 = torch.empty(int(desc3["offset"][-1] + desc3["n"][-1]) + 64, device="cuda")
+    nr.nrng_batched_autotune(out3, nr.descriptors_to_device(desc3), len(desc3), ws3, "accurate", reps=1)
+    assert len(cache.read_text().splitlines()) == 2
+    nr.nrng_batched_set_config(torch.float32, "accurate", -1)
+
+
 def test_batched_device_descriptor_errors():
     wl, desc, d_desc, out, ws = make_batch(8, 10, 1000, "mixed", align=1)
     bad = desc.copy()

@@ -159,9 +159,9 @@ def test_batched_workspace_size(lib):
     assert lib.nrng_batched_workspace_size(d.ctypes.data_as(ctypes.c_void_p), len(d), ctypes.byref(b)) == _lib.OK
     k = len(d)
     fixed = (64 + (k + 1) * 8 + k * 8 + k * 4 + 255) // 256 * 256
-    # most slots over the configurations: the smallest Polar tile has 2*256*2 = 1024 candidates
+    # most slots over the configurations: the smallest Polar tile has 2*128*4 = 1024 candidates
     worst = 0
-    for threads, bpt in [(256, 4), (256, 8), (128, 8), (512, 4), (128, 4), (512, 2)]:
+    for threads, bpt in [(128, 16), (128, 12), (128, 8), (256, 8), (128, 4), (256, 4)]:
         cand = 2 * threads * bpt
         s = 0
         for n in (1000, 5000):
@@ -204,7 +204,7 @@ def test_config_table(lib):
     assert lib.nrng_batched_set_config(0, 1, 4) == _lib.OK
     assert lib.nrng_batched_get_config(0, 1, ctypes.byref(c)) == _lib.OK and c.value == 4
     assert lib.nrng_batched_set_config(0, 1, -1) == _lib.OK
-    assert lib.nrng_batched_get_config(0, 1, ctypes.byref(c)) == _lib.OK and c.value == 1
+    assert lib.nrng_batched_get_config(0, 1, ctypes.byref(c)) == _lib.OK and c.value == 0   # default 128 x 16
     assert lib.nrng_batched_set_config(0, 1, 99) == _lib.ERR_INVALID_VALUE
 
 
@@ -245,5 +245,5 @@ def test_force_config_env():
                              timeout=300)
         assert out.returncode == 0, out.stderr
         got = int(out.stdout.strip())
-        assert got == (want if want is not None else 1), (env_val, got)
+        assert got == (want if want is not None else 0), (env_val, got)
 

@@ -168,7 +168,8 @@ int32_t nrng_polar_twopass(void *d_out, int64_t n, float mu, float sigma, uint64
  * j mod 4 of block counter + j/4), u_i = (w >> 8) 2^-24.  With
  * m = max(u1, u2) and u = m^2 (uniform on [0, 1)), r = sigma sqrt(-ln(1 - u))
  * is computed as sigma m h(v) by a fitted polynomial h of
- * v = (6u - 4)/(4 - 3u) for u <= 8/9 and by logf above, and theta =
+ * v = (6u - 4)/(4 - 3u) for u <= 8/9 and by the hardware log2 and square
+ * root above (the library step of the paper), and theta =
  * 2 pi u3 - pi by Method B2's sine and cosine polynomials with double-angle
  * steps.  d_out[2p] = sqrt(2) r cos(theta) + mu, d_out[2p + 1] =
  * sqrt(2) r sin(theta) + mu.  Uses 3 ceil(n/8) blocks from `counter` (eight
@@ -183,7 +184,8 @@ int32_t nrng_boxmuller_b3(void *d_out, int64_t n, float mu, float sigma, uint64_
  * d_out[2i] = r x + mu, d_out[2i + 1] = r y + mu.  1 - s is uniform and
  * independent of the angle, so this is also a normal pair, different from
  * nrng_polar's.  ln(1 - s)/s comes from the polynomial h of Method B3 for
- * s <= 8/9 (no logarithm, no division) and from logf above.  Workspace,
+ * s <= 8/9 (no logarithm, no division) and from the hardware log2,
+ * reciprocal and square root of the exact 1 - s above.  Workspace,
  * counter use, d_next_counter and d_pair_candidate: as nrng_polar (size it
  * with nrng_polar_workspace_size).  Error within 2e-5 max(1, |z|). */
 int32_t nrng_polar_p2(void *d_out, int64_t n, float mu, float sigma, uint64_t key,

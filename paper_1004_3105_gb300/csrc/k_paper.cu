@@ -3,8 +3,8 @@
 //
 // B3 draws three uniforms per pair (u1, u2, u3), takes u = max(u1, u2)^2 so
 // that sqrt(u) = max(u1, u2) needs no square root, evaluates
-// sqrt(-ln(1 - u) / u) by the polynomial h(v) for u <= 8/9 (library logf
-// above), and the sine and cosine of 2 pi u3 - pi by Method B2's polynomials
+// sqrt(-ln(1 - u) / u) by the polynomial h(v) for u <= 8/9 (the hardware
+// log2 and square root above), and the sine and cosine of 2 pi u3 - pi by Method B2's polynomials
 // and double-angle steps.  One thread takes four pairs: twelve words, three
 // Philox blocks, eight outputs.  The paper gathers the u > 8/9 cases into a
 // list vector; here they are a divergent branch within the warp.
@@ -29,7 +29,9 @@ __device__ __forceinline__ void b3_pair(uint32_t w1, uint32_t w2, uint32_t w3, f
     const float u = m * m;
     float rs;   // r sqrt2 = sigma sqrt(-2 ln(1 - u))
     if (u > 0.888888888f) {
-        rs = sigma * sqrtf(-2.0f * logf(fmaf(-m, m, 1.0f)));   // 1 - m^2 with one rounding
+        // 1 - m^2 with one rounding; |log2| > 3.1 there, so the hardware log2
+        // and square root keep their relative accuracy (near 2^-22)
+        rs = sigma * sqrt_approx(__log2f(fmaf(-m, m, 1.0f)) * -1.38629436f);
     } else {
         rs = sigma * 1.41421356f * m * h_of_u(u);
     }

@@ -395,6 +395,22 @@ def check_ws(nr, ws):
         raise RuntimeError(f"device status {nr._lib.STATUS.get(st, st)}")
 
 
+def timed_launches(run, K):
+    """Mean ms per launch over K back-to-back launches (events around the
+    whole run), plus the median and minimum of the per-launch times (an event
+    between consecutive launches)."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ev[0].record()
+    for i in range(K):
+        run()
+        ev[i + 1].record()
+    torch.cuda.synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
+    return ev[0].elapsed_time(ev[K]) / K, {"ms_median": round(float(np.median(per)), 4),
+                                            "ms_min": round(float(np.min(per)), 4)}
+
+
 def precision_sweep(step, K, W, peak):
     """{B1, Polar} x {accurate, fast} x {f32, bf16, f16} at N = 2^28, then
     Methods B2, B3, P2, R and the two-pass Polar in f32."""
@@ -416,17 +432,12 @@ def precision_sweep(step, K, W, peak):
                     run()
                     if method == "polar":
                         check_ws(nr, step.ws_p)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(K):
-                    run()
-                e1.record()
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / K
+                ms, stats = timed_launches(run, K)
                 by = N_FULL * buf.element_size()
                 gbs = by / (ms * 1e-3) / 1e9
                 out[f"{method}_{mode}_{names[dt]}"] = {"ms": round(ms, 4), "normals_per_s": N_FULL / (ms * 1e-3),
-                                                       "GB_per_s": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4)}
+                                                       "GB_per_s": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4),
+                                                       **stats}
     # the paper's further methods and the two-pass Polar, f32, same N
     ws_r = torch.empty(nr.nrng_ratio_workspace_size(N_FULL), dtype=torch.uint8, device=step.out_b1.device)
     ws_2 = torch.empty(nr.nrng_polar_twopass_workspace_size(N_FULL), dtype=torch.uint8, device=step.out_b1.device)
@@ -447,16 +458,10 @@ def precision_sweep(step, K, W, peak):
             run()
             if name in checked_ws:
                 check_ws(nr, checked_ws[name])
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(K):
-            run()
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / K
+        ms, stats = timed_launches(run, K)
         gbs = N_FULL * 4 / (ms * 1e-3) / 1e9
         out[name] = {"ms": round(ms, 4), "normals_per_s": N_FULL / (ms * 1e-3), "GB_per_s": round(gbs, 1),
-                     "frac_of_hbm": round(gbs / peak, 4)}
+                     "frac_of_hbm": round(gbs / peak, 4), **stats}
     for ws in (ws_r, ws_2):
         st = nr.nrng_get_status(ws)
         if st != 0:

@@ -205,6 +205,11 @@ class ClockSampler:
                 "reasons": sorted(self.reasons), "samples": len(self.samples), "source": "nvml"}
 
 
+def sm_count_of(dev) -> int:
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
 def bind_to_gpu_cpus(cuda_index: int):
     """Restricts this process to the host CPUs NVML reports as closest to the
     GPU (read only: a process setting, nothing on the GPU changes), so that
@@ -287,6 +292,10 @@ class Step:
             self.h_w2 = torch.from_numpy(2.0 * rw.w).pin_memory()
             self.h_desc = torch.from_numpy(desc.view(np.uint8).copy()).pin_memory()
         self.normals_per_step = 2 * N_FULL + self.batch_total + self.n_rep
+        # algorithmic Philox blocks of the batched launch: n/4 per B1 stream,
+        # n/pi per Polar stream
+        self.batch_philox_blocks = float(sum(int(n) / 4 if m == 0 else int(n) / math.pi
+                                             for n, m in zip(wl.n, wl.method)))
         # our kernels per step: B1 1, Polar 1, batched 2 (prep + main), reparam fwd + bwd 2
         self.our_launches_per_step = 6
 
@@ -701,6 +710,17 @@ def bench_ours(args):
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
                 "traffic": recorded_traffic(kernel_names[dom]),
                 "algorithmic_bytes_per_launch": alg_bytes[dom]}
+    # The same kernel against the Philox multiply floor: 20 32x32->64 products
+    # a block at 64 products a clock per SM (two per wide product) is 1.6
+    # blocks a clock per SM.  Algorithmic blocks: n/4 per B1 stream, n/pi per
+    # Polar stream (n/2 pairs at acceptance pi/4, two candidates a block).
+    sm_mhz = clocks.summary().get("sm_mhz") or 2070.0
+    floor = sm_count_of(torch.cuda.current_device()) * sm_mhz * 1e6 * 1.6
+    alg_blocks = {"b1": N_FULL / 4, "polar": N_FULL / math.pi, "batch": step.batch_philox_blocks}
+    roofline_philox = {"kernel": kernel_names[dom], "bound": "alu", "unit": "Philox blocks/s",
+                       "achieved": alg_blocks[dom] / t_dom, "peak": floor,
+                       "frac": round(alg_blocks[dom] / t_dom / floor, 4),
+                       "peak_source": f"derived: SMs x {sm_mhz:.0f} MHz x 1.6 blocks/clock/SM"}
 
     # ---- precision sweep at N = 2^28 (mu 1.5, sigma 0.25): each variant timed
     # alone with CUDA events (mean of K launches after W warm-ups), not part of
@@ -727,6 +747,7 @@ def bench_ours(args):
                        "l2": "every output > L2 (1 GiB per single-stream kernel); no flush",
                        "parallelism": f"replicas x{world}"},
             "parts": parts, "sweep": sweep, "write_ceiling": ceiling, "roofline": roofline,
+            "roofline_philox": roofline_philox,
             "clocks": clocks.summary(),
             "e2e": e2e, "gpu_launches": K * step.our_launches_per_step, "cpu_baseline": cpu,
         }

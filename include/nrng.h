@@ -217,17 +217,35 @@ int32_t nrng_ratio(void *d_out, int64_t n, float mu, float sigma, uint64_t key,
                    uint64_t *d_next_counter, int64_t *d_candidate, nrng_stream_t stream);
 
 /* Diagnostics (no counterpart in the paper): the per-pair transforms at
- * caller-given inputs, so that tests reach lattice points a stream reaches
- * too rarely (s -> 1, S = 1, u = 0, u = 1 - 2^-24, the quadrant angles).
- * kind 0 (NRNG_B1): d_in holds n pairs of 32-bit Philox words (wu, wv);
- *   d_out[2i], d_out[2i + 1] receive B1's x, y for that pair, exactly as
- *   nrng_boxmuller computes them (mode NRNG_ACCURATE, NRNG_FAST or NRNG_B2).
- * kind 1 (NRNG_POLAR): d_in holds n pairs of int32 lattice coordinates
- *   (kx', ky') in [-2^23, 2^23); d_accept[i] (nullable) receives Algorithm P's
- *   step-3 decision (1 iff 0 < S < 2^46) and d_out[2i], d_out[2i + 1] step 4's
- *   values as nrng_polar computes them, meaningful only where accepted
- *   (mode NRNG_ACCURATE or NRNG_FAST).
- * d_in: 2n x 4 bytes, 4-byte aligned; d_out: 2n floats; d_accept: n int32. */
+ * caller-given inputs, so that tests reach points a stream reaches too
+ * rarely (s -> 1, S = 1, u = 0, u = 1 - 2^-24, the quadrant angles, the
+ * switch to the upper branch at 8/9, the accept boundary of R).  Each kind
+ * computes exactly what its generator computes for that input:
+ * kind NRNG_POINTS_B1: d_in holds n pairs of 32-bit Philox words (wu, wv);
+ *   d_out[2i], d_out[2i + 1] receive B1's x, y (nrng_boxmuller; mode
+ *   NRNG_ACCURATE, NRNG_FAST or NRNG_B2).
+ * kind NRNG_POINTS_POLAR: d_in holds n pairs of int32 lattice coordinates
+ *   (kx', ky') in [-2^23, 2^23); d_accept[i] receives Algorithm P's step-3
+ *   decision (1 iff 0 < S < 2^46) and d_out[2i], d_out[2i + 1] step 4's
+ *   values (nrng_polar; mode NRNG_ACCURATE or NRNG_FAST), meaningful only
+ *   where accepted.
+ * kind NRNG_POINTS_P2: as NRNG_POINTS_POLAR with Method P2's step 4a
+ *   (nrng_polar_p2; mode NRNG_ACCURATE or NRNG_FAST, which give the same
+ *   values).
+ * kind NRNG_POINTS_RATIO: d_in holds n pairs of Philox words (wu, wv);
+ *   d_accept[i] receives Algorithm R's step-3 decision, d_out[2i] step 4's
+ *   value (nrng_ratio; mode NRNG_ACCURATE or NRNG_FAST), meaningful only
+ *   where accepted, and d_out[2i + 1] = 0.
+ * kind NRNG_POINTS_B3: d_in holds n triples of Philox words (w1, w2, w3);
+ *   d_out[2i], d_out[2i + 1] receive Method B3's pair (nrng_boxmuller_b3;
+ *   mode NRNG_ACCURATE or NRNG_FAST, which give the same values).
+ * d_accept (nullable) receives 1 for every point of kinds B1 and B3.
+ * d_in: 2n x 4 bytes (3n x 4 bytes for B3), 4-byte aligned; d_out: 2n
+ * floats; d_accept: n int32.  Returns NRNG_ERR_INVALID_VALUE for an unknown
+ * kind or a mode the kind does not take. */
+typedef enum {
+    NRNG_POINTS_B1 = 0, NRNG_POINTS_POLAR = 1, NRNG_POINTS_P2 = 2, NRNG_POINTS_RATIO = 3, NRNG_POINTS_B3 = 4
+} nrng_points_kind_t;
 int32_t nrng_eval_points(int32_t kind, int32_t mode, const void *d_in, int64_t n, float mu, float sigma,
                          float *d_out, int32_t *d_accept, nrng_stream_t stream);
 

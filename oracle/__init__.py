@@ -16,10 +16,10 @@ Functions and the passages they follow (paper: Brent, TR-CS-93-04, 1993):
   polar_accept_points
   lattice_accept_count           exact acceptance count of P's step 3
   batched                        independent B1/P streams
-  b3                             Sec. 3, Method B3 (exact function for h)
-  polar_p2                       Sec. 4, Method P2 (step 4a, exact function for h)
+  b3, b3_points                  Sec. 3, Method B3 (exact function for h)
+  polar_p2, p2_points            Sec. 4, Method P2 (step 4a, exact function for h)
   ratio, ratio_candidates,       Sec. 5, Algorithm R (ratio-of-uniforms region)
-  ratio_at
+  ratio_at, ratio_points
   reparam_fwd, reparam_bwd       x = mu + sigma z with z from B1, and its
                                  gradients (an add-on; no counterpart in the paper)
 """
@@ -76,6 +76,9 @@ def _load():
         "orc_lattice_accept_count": (i64, []),
         "orc_batched": (None, [P, i32, P, P, P, P, P, P, P]),
         "orc_b3": (None, [P, i64, f64, f64, u64, u64]),
+        "orc_b3_points": (None, [P, P, P, P, i64, f64, f64]),
+        "orc_p2_points": (None, [P, P, P, i64, f64, f64]),
+        "orc_ratio_points": (None, [P, P, P, P, i64, f64, f64]),
         "orc_polar_p2": (i64, [P, i64, f64, f64, u64, u64, P, P]),
         "orc_ratio": (i64, [P, i64, f64, f64, u64, u64, P, P]),
         "orc_ratio_candidates": (None, [P, i64, u64, u64]),
@@ -203,6 +206,23 @@ def b3(n: int, mu: float, sigma: float, key: int, counter: int) -> np.ndarray:
     return out
 
 
+def b3_points(u1, u2, u3, mu: float, sigma: float) -> np.ndarray:
+    """Method B3's pair at given uniforms, shape [m, 2]."""
+    u1, u2, u3 = (np.ascontiguousarray(a, dtype=np.float64) for a in (u1, u2, u3))
+    out = np.zeros((u1.size, 2), dtype=np.float64)
+    _load().orc_b3_points(_ptr(out), _ptr(u1), _ptr(u2), _ptr(u3), u1.size, float(mu), float(sigma))
+    return out
+
+
+def p2_points(kx, ky, mu: float, sigma: float) -> np.ndarray:
+    """Method P2's step 4a at given accepted lattice points, shape [m, 2]."""
+    kx = np.ascontiguousarray(kx, dtype=np.int32)
+    ky = np.ascontiguousarray(ky, dtype=np.int32)
+    out = np.zeros((kx.size, 2), dtype=np.float64)
+    _load().orc_p2_points(_ptr(out), _ptr(kx), _ptr(ky), kx.size, float(mu), float(sigma))
+    return out
+
+
 def polar_p2(n: int, mu: float, sigma: float, key: int, counter: int):
     """Method P2 (Sec. 4, step 4a); returns (out, pair_candidate, next_counter, candidates)."""
     npairs = (n + 1) // 2
@@ -234,6 +254,17 @@ def ratio_at(cand, mu: float, sigma: float, key: int, counter: int) -> np.ndarra
     out = np.zeros(cand.size, dtype=np.float64)
     _load().orc_ratio_at(_ptr(out), _ptr(cand), cand.size, float(mu), float(sigma), _u64(key), _u64(counter))
     return out
+
+
+def ratio_points(u, v, mu: float, sigma: float):
+    """Algorithm R's steps 2-4 at given uniforms; returns (accept uint8 [m],
+    values [m], meaningful where accepted)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros(u.size, dtype=np.float64)
+    acc = np.zeros(u.size, dtype=np.uint8)
+    _load().orc_ratio_points(_ptr(out), _ptr(acc), _ptr(u), _ptr(v), u.size, float(mu), float(sigma))
+    return acc, out
 
 
 def batched(total: int, desc: dict) -> np.ndarray:

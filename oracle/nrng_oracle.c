@@ -319,19 +319,33 @@ static uint32_t orc_word(int64_t i, uint64_t key, uint64_t counter)
  *   step 3: r = sigma sqrt(-ln(1 - u));
  *   step 4: s = sin(2 pi u3 - pi), c = cos(2 pi u3 - pi);
  *   step 5: return mu + c r sqrt2 and mu + s r sqrt2 (out[2p], out[2p+1]). */
+static void orc_b3_pair(double u1, double u2, double u3, double mu, double sigma, double *x, double *y)
+{
+    double m = (u1 > u2) ? u1 : u2;
+    double u = m * m;                       /* exact: m has 24 bits */
+    double r = sigma * sqrt(-log(1.0 - u));
+    double a = 2.0 * M_PI * u3 - M_PI;
+    *x = mu + cos(a) * r * sqrt(2.0);
+    *y = mu + sin(a) * r * sqrt(2.0);
+}
+
 void orc_b3(double *out, int64_t n, double mu, double sigma, uint64_t key, uint64_t counter)
 {
     for (int64_t p = 0; 2 * p < n; ++p) {
-        double u1 = orc_u24(orc_word(3 * p, key, counter));
-        double u2 = orc_u24(orc_word(3 * p + 1, key, counter));
-        double u3 = orc_u24(orc_word(3 * p + 2, key, counter));
-        double m = (u1 > u2) ? u1 : u2;
-        double u = m * m;                       /* exact: m has 24 bits */
-        double r = sigma * sqrt(-log(1.0 - u));
-        double a = 2.0 * M_PI * u3 - M_PI;
-        out[2 * p] = mu + cos(a) * r * sqrt(2.0);
-        if (2 * p + 1 < n) out[2 * p + 1] = mu + sin(a) * r * sqrt(2.0);
+        double x, y;
+        orc_b3_pair(orc_u24(orc_word(3 * p, key, counter)), orc_u24(orc_word(3 * p + 1, key, counter)),
+                    orc_u24(orc_word(3 * p + 2, key, counter)), mu, sigma, &x, &y);
+        out[2 * p] = x;
+        if (2 * p + 1 < n) out[2 * p + 1] = y;
     }
+}
+
+/* Steps 2-5 at given uniforms (for hand-picked cases). */
+void orc_b3_points(double *out2, const double *u1, const double *u2, const double *u3, int64_t m, double mu,
+                   double sigma)
+{
+    for (int64_t j = 0; j < m; ++j)
+        orc_b3_pair(u1[j], u2[j], u3[j], mu, sigma, &out2[2 * j], &out2[2 * j + 1]);
 }
 
 /* ------------------------------------------------- Method P2 (Sec 4, 4a) */
@@ -347,6 +361,14 @@ static void orc_p2_step4(int32_t kx, int32_t ky, double mu, double sigma, double
     double r = sigma * sqrt(-log(1.0 - s) / s);
     *ox = x * r * sqrt(2.0) + mu;
     *oy = y * r * sqrt(2.0) + mu;
+}
+
+/* Step 4a at given lattice points (for hand-picked cases); the caller keeps
+ * to accepted points (0 < S < 2^46). */
+void orc_p2_points(double *out2, const int32_t *kx, const int32_t *ky, int64_t m, double mu, double sigma)
+{
+    for (int64_t j = 0; j < m; ++j)
+        orc_p2_step4(kx[j], ky[j], mu, sigma, &out2[2 * j], &out2[2 * j + 1]);
 }
 
 /* Method P2: the candidate stream, acceptance and compaction of Algorithm P,
@@ -435,6 +457,18 @@ void orc_ratio_at(double *out, const int64_t *cand, int64_t m, double mu, double
         double u, v, x;
         orc_ratio_candidate(cand[j], key, counter, &u, &v);
         orc_ratio_accept(u, v, &x);
+        out[j] = sigma * x + mu;
+    }
+}
+
+/* Steps 2-4 of R at given uniforms (for hand-picked cases): accept[j] is
+ * step 3's decision, out[j] = sigma x + mu (meaningful where accepted). */
+void orc_ratio_points(double *out, uint8_t *accept, const double *u, const double *v, int64_t m, double mu,
+                      double sigma)
+{
+    for (int64_t j = 0; j < m; ++j) {
+        double x;
+        accept[j] = (uint8_t)orc_ratio_accept(u[j], v[j], &x);
         out[j] = sigma * x + mu;
     }
 }

@@ -6,7 +6,8 @@ uniforms, as hand-written sm_103a CUDA kernels behind the C ABI of
 include/nrng.h.  The binding functions carry the C entry points' names."""
 from ._lib import NrngError, load  # noqa: F401
 from .nrng import (  # noqa: F401
-    ACCURATE, B1, B2, FAST, POLAR, STREAM_DESC, BatchedGraph, Reparam, broadcast_layout, descriptors_to_device,
+    ACCURATE, B1, B2, FAST, POINTS_B3, POINTS_P2, POINTS_RATIO, POLAR, STREAM_DESC, BatchedGraph, Reparam,
+    broadcast_layout, descriptors_to_device,
     nrng_batched, nrng_batched_autotune, nrng_batched_config_count, nrng_batched_config_info,
     nrng_batched_get_config, nrng_batched_set_config, nrng_batched_workspace_size, nrng_boxmuller,
     nrng_boxmuller_b3, nrng_eval_points, nrng_get_status, nrng_polar, nrng_polar_max_blocks, nrng_polar_noalloc, nrng_polar_p2,

@@ -445,8 +445,8 @@ int32_t nrng_eval_points(int32_t kind, int32_t mode, const void *d_in, int64_t n
                          float *d_out, int32_t *d_accept, nrng_stream_t stream)
 {
     const CallRange range("nrng_eval_points");
-    if (kind != NRNG_B1 && kind != NRNG_POLAR) return NRNG_ERR_INVALID_VALUE;
-    if (!(valid_mode(mode) || (mode == NRNG_B2 && kind == NRNG_B1))) return NRNG_ERR_INVALID_VALUE;
+    if (kind < NRNG_POINTS_B1 || kind > NRNG_POINTS_B3) return NRNG_ERR_INVALID_VALUE;
+    if (!(valid_mode(mode) || (mode == NRNG_B2 && kind == NRNG_POINTS_B1))) return NRNG_ERR_INVALID_VALUE;
     if (n < 0 || (n > 0 && (d_in == nullptr || d_out == nullptr))) return NRNG_ERR_INVALID_VALUE;
     if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
     if ((uintptr_t)d_in % 4 || (uintptr_t)d_out % 4 || (uintptr_t)d_accept % 4) return NRNG_ERR_MISALIGNED;

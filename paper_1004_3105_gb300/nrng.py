@@ -18,6 +18,8 @@ from ._lib import NrngError, check, load
 
 ACCURATE, FAST, B2 = 0, 1, 2
 B1, POLAR = 0, 1
+# kinds of nrng_eval_points (B1 and POLAR double as the first two)
+POINTS_P2, POINTS_RATIO, POINTS_B3 = 2, 3, 4
 _MODES = {"accurate": ACCURATE, "fast": FAST, "b2": B2, ACCURATE: ACCURATE, FAST: FAST, B2: B2}
 _DTYPES = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
 
@@ -199,12 +201,14 @@ def nrng_ratio(out: torch.Tensor, mu: float, sigma: float, key: int, counter: in
 
 def nrng_eval_points(kind: int, points: torch.Tensor, mu: float = 0.0, sigma: float = 1.0, mode="accurate",
                      stream=None):
-    """The per-pair transform at given inputs (diagnostics).  kind B1: points
-    is an [n, 2] uint32/int32 tensor of Philox words (wu, wv); kind POLAR: an
-    [n, 2] int32 tensor of lattice coordinates (kx', ky').  Returns (values
-    [n, 2] float32, accept [n] int32)."""
-    if points.dim() != 2 or points.shape[1] != 2 or points.element_size() != 4:
-        raise ValueError("points must be an [n, 2] tensor of 32-bit words")
+    """The per-pair transform at given inputs (diagnostics).  kind B1 and
+    POINTS_RATIO: points is an [n, 2] uint32/int32 tensor of Philox words
+    (wu, wv); POLAR and POINTS_P2: an [n, 2] int32 tensor of lattice
+    coordinates (kx', ky'); POINTS_B3: an [n, 3] tensor of words (w1, w2, w3).
+    Returns (values [n, 2] float32, accept [n] int32)."""
+    width = 3 if kind == POINTS_B3 else 2
+    if points.dim() != 2 or points.shape[1] != width or points.element_size() != 4:
+        raise ValueError(f"points must be an [n, {width}] tensor of 32-bit words")
     pts = points.contiguous()
     n = pts.shape[0]
     out = torch.empty((n, 2), dtype=torch.float32, device=pts.device)

@@ -211,7 +211,12 @@ def test_config_table(lib):
 def test_eval_points_validation(lib):
     f = lib.nrng_eval_points
     assert f(7, 0, FAKE, 4, 0.0, 1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE      # kind
-    assert f(1, 2, FAKE, 4, 0.0, 1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE      # B2 is a B1 mode
+    assert f(5, 0, FAKE, 4, 0.0, 1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE
+    assert f(-1, 0, FAKE, 4, 0.0, 1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE
+    for kind in (1, 2, 3, 4):                                                           # B2 is a B1 mode
+        assert f(kind, 2, FAKE, 4, 0.0, 1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE
+    for kind in (2, 3, 4):
+        assert f(kind, 0, None, 0, 0.0, 1.0, None, None, None) == _lib.OK
     assert f(0, 5, FAKE, 4, 0.0, 1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE
     assert f(0, 0, None, 4, 0.0, 1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE
     assert f(0, 0, FAKE, 4, 0.0, -1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE

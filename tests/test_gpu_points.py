@@ -1,13 +1,16 @@
 """The per-pair transforms at hand-picked lattice points, through
 nrng_eval_points, against the oracle: the special points of Algorithm B1
 (u = 0, u = 1 - 2^-24, v on the quadrant angles) and of Algorithm P
-(S = 1, S = 2, S just below and at 2^46, s -> 1, the origin), which a stream
-reaches too rarely to test.  Accept decisions bit-exact; values within the
-mode's tolerance."""
+(S = 1, S = 2, S just below and at 2^46, s -> 1, the origin), Method P2's and
+B3's switch to the upper branch at 8/9, and the lattice points next to
+Algorithm R's accept boundary, which a stream reaches too rarely to test.
+Accept decisions bit-exact (for R, wherever the boundary is farther than
+1e-12 relative); values within the mode's tolerance."""
 import numpy as np
 import pytest
 import torch
 
+import lattice_points as LP
 import oracle
 import paper_1004_3105_gb300 as nr
 from gpu_helpers import assert_close
@@ -81,11 +84,73 @@ def test_polar_special_points(mode):
                  f"Polar points {mode}")
 
 
+def test_p2_special_points():
+    p, S = LP.p2_points()
+    pts = torch.from_numpy(p).cuda()
+    got, acc = nr.nrng_eval_points(nr.POINTS_P2, pts, MU, SIGMA, "accurate")
+    got_fast, _ = nr.nrng_eval_points(nr.POINTS_P2, pts, MU, SIGMA, "fast")
+    # one mode: bit-identical values (NaN at rejected points, where they are meaningless)
+    torch.testing.assert_close(got, got_fast, rtol=0, atol=0, equal_nan=True)
+    acc = acc.cpu().numpy()
+    assert np.array_equal(acc, ((S > 0) & (S < LP.S_ONE)).astype(np.int32)), "accept decisions"
+    # both sides of the switch at 8/9 are reached closely, and s -> 1
+    assert ((S > LP.S_SWITCH) & (S < LP.S_SWITCH + 10 ** 8)).sum() > 1000
+    assert ((S <= LP.S_SWITCH) & (S > LP.S_SWITCH - 10 ** 8)).sum() > 1000
+    assert ((S < LP.S_ONE) & (S > LP.S_ONE - 10 ** 9)).sum() > 1000
+    keep = np.flatnonzero(acc == 1)
+    ref = oracle.p2_points(p[keep, 0], p[keep, 1], MU, SIGMA)
+    assert_close(got[torch.from_numpy(keep).cuda()].reshape(-1), ref.reshape(-1), MU, SIGMA, "fast", "P2 points")
+
+
+@pytest.mark.parametrize("mode", ["accurate", "fast"])
+def test_ratio_boundary_points(mode):
+    w = LP.ratio_words()
+    got, acc = nr.nrng_eval_points(nr.POINTS_RATIO, torch.from_numpy(w.view(np.int32)).cuda(), MU, SIGMA, mode)
+    k = (w[:, 0] >> 8).astype(np.int64)
+    j = (w[:, 1] >> 8).astype(np.int64)
+    want, ref = oracle.ratio_points(k * 2.0 ** -24, j * 2.0 ** -24, MU, SIGMA)
+    acc = acc.cpu().numpy()
+    gap = LP.ratio_relative_gap(k, j)
+    # most points lie inside the float screen's margin, so the double
+    # decision takes them; within 1e-12 of the boundary (a handful of points
+    # at the region's widest place) double rounding may decide either way
+    assert (gap < 1e-5).sum() > 20000
+    decided = gap >= 1e-12
+    assert np.array_equal(acc[decided], want[decided].astype(np.int32)), "accept decisions"
+    assert acc.sum() > 10000 and (acc == 0).sum() > 10000
+    keep = np.flatnonzero((acc == 1) & (want == 1))
+    assert_close(got[torch.from_numpy(keep).cuda(), 0], ref[keep], MU, SIGMA, mode, f"R points {mode}")
+    assert bool((got[:, 1] == 0).all())
+
+
+def test_b3_special_points():
+    w = LP.b3_words()
+    pts = torch.from_numpy(w.view(np.int32)).cuda()
+    got, acc = nr.nrng_eval_points(nr.POINTS_B3, pts, MU, SIGMA, "accurate")
+    got_fast, _ = nr.nrng_eval_points(nr.POINTS_B3, pts, MU, SIGMA, "fast")
+    torch.testing.assert_close(got, got_fast, rtol=0, atol=0)   # one mode
+    assert bool((acc == 1).all())
+    ref = oracle.b3_points(LP.u24(w[:, 0]), LP.u24(w[:, 1]), LP.u24(w[:, 2]), MU, SIGMA)
+    assert_close(got.reshape(-1), ref.reshape(-1), MU, SIGMA, "fast", "B3 points")
+    m = np.maximum(w[:, 0] >> 8, w[:, 1] >> 8).astype(np.float64) * 2.0 ** -24
+    assert (m * m > 8.0 / 9.0).sum() > 500 and ((m * m <= 8.0 / 9.0) & (m * m > 0.8888)).sum() > 500
+    # u1 = u2 = 0 gives r = 0: both outputs are exactly mu
+    z = m == 0
+    assert z.any() and np.all(got.cpu().numpy()[z] == np.float32(MU))
+
+
 def test_eval_points_validation():
     pts = torch.zeros((4, 2), dtype=torch.int32, device="cuda")
     with pytest.raises(nr.NrngError):
         nr.nrng_eval_points(7, pts)
     with pytest.raises(nr.NrngError):
-        nr.nrng_eval_points(nr.POLAR, pts, mode="b2")
+        nr.nrng_eval_points(5, pts)
+    for kind in (nr.POLAR, nr.POINTS_P2, nr.POINTS_RATIO):
+        with pytest.raises(nr.NrngError):
+            nr.nrng_eval_points(kind, pts, mode="b2")
+    with pytest.raises(ValueError):
+        nr.nrng_eval_points(nr.POINTS_B3, pts)
     out, acc = nr.nrng_eval_points(nr.POLAR, pts[:0])
+    assert out.shape == (0, 2) and acc.shape == (0,)
+    out, acc = nr.nrng_eval_points(nr.POINTS_B3, torch.zeros((0, 3), dtype=torch.int32, device="cuda"))
     assert out.shape == (0, 2) and acc.shape == (0,)

@@ -49,6 +49,31 @@ def test_b1_special_points(mode):
     assert np.all(z == np.float32(MU))
 
 
+def test_b1_accurate_every_lattice_radius_and_angle():
+    """The accurate B1 transform over its whole domain: every radius k (2^24
+    values, at t = 0, where sin = 0 and cos = 1 exactly, so y = r) and every
+    angle t (2^24 values, at u = 1 - e^-1/2, where r is near 1), against the
+    oracle.  r within 4e-7 of itself; x, y within 3e-7 absolute at r ~ 1."""
+    n = 1 << 24
+    idx = np.arange(n, dtype=np.uint64)
+    w = np.stack([(idx << np.uint64(8)).astype(np.uint32), np.zeros(n, np.uint32)], axis=1)
+    got, _ = nr.nrng_eval_points(nr.B1, torch.from_numpy(w.view(np.int32)).cuda(), 0.0, 1.0, "accurate")
+    g = got.cpu().numpy().astype(np.float64)
+    u = idx.astype(np.float64) * 2.0 ** -24
+    ref = oracle.b1_points(u, np.zeros(n), 0.0, 1.0)
+    assert np.all(g[:, 0] == 0.0)
+    assert g[0, 1] == 0.0                                   # u = 0: r = 0
+    rel = np.abs(g[1:, 1] - ref[1:, 1]) / ref[1:, 1]
+    assert rel.max() <= 4e-7, f"radius: max relative error {rel.max():.3e} at k = {int(np.argmax(rel)) + 1}"
+    k0 = int(LP.M24 * (1.0 - np.exp(-0.5)))
+    w = np.stack([np.full(n, k0 << 8, np.uint32), (idx << np.uint64(8)).astype(np.uint32)], axis=1)
+    got, _ = nr.nrng_eval_points(nr.B1, torch.from_numpy(w.view(np.int32)).cuda(), 0.0, 1.0, "accurate")
+    g = got.cpu().numpy().astype(np.float64)
+    ref = oracle.b1_points(np.full(n, k0 * 2.0 ** -24), u, 0.0, 1.0)
+    err = np.abs(g - ref).max()
+    assert err <= 3e-7, f"angle: max absolute error {err:.3e}"
+
+
 def polar_points():
     m = 1 << 23
     pts = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, -1), (3, 4),

@@ -92,6 +92,25 @@ def polar_points():
     return np.array(pts, dtype=np.int32)
 
 
+def test_polar_accurate_radius():
+    """ln s of the accurate Polar path at every S = k^2 (0 < k < 2^23, so s
+    runs from 2^-46 to 1 - 2^-22) and at 4 M random lattice points: the
+    radius |(x, y) - mu| within 5e-7 of itself against the oracle."""
+    k = np.arange(1, 1 << 23, dtype=np.int64)
+    rng = np.random.Generator(np.random.PCG64(21))
+    rnd = rng.integers(-(1 << 23), 1 << 23, (1 << 22, 2))
+    p = np.concatenate([np.stack([k, np.zeros_like(k)], axis=1), rnd]).astype(np.int32)
+    S = p[:, 0].astype(np.int64) ** 2 + p[:, 1].astype(np.int64) ** 2
+    p = p[(S > 0) & (S < (1 << 46))]
+    got, acc = nr.nrng_eval_points(nr.POLAR, torch.from_numpy(p).cuda(), 0.0, 1.0, "accurate")
+    assert bool((acc == 1).all())
+    g = got.cpu().numpy().astype(np.float64)
+    ref = oracle.polar_points(p[:, 0], p[:, 1], 0.0, 1.0)
+    r_got, r_ref = np.hypot(g[:, 0], g[:, 1]), np.hypot(ref[:, 0], ref[:, 1])
+    rel = np.abs(r_got - r_ref) / r_ref
+    assert rel.max() <= 5e-7, f"max relative radius error {rel.max():.3e} at {p[int(np.argmax(rel))]}"
+
+
 @pytest.mark.parametrize("mode", ["accurate", "fast"])
 def test_polar_special_points(mode):
     p = polar_points()

@@ -592,6 +592,94 @@ def cpu_oracle_sample(seconds_budget: float = 12.0):
                 "seconds": one["seconds"]}
 
 
+def timed_flushed(run, K, flush):
+    """Median and minimum ms of K launches, each after an L2 flush (outside
+    the events): for outputs that fit in L2."""
+    import torch
+    per = []
+    for _ in range(K):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        per.append(e0.elapsed_time(e1))
+    return float(np.median(per)), {"ms_median": round(float(np.median(per)), 4), "ms_min": round(float(np.min(per)), 4)}
+
+
+def configs_sweep(step, K, warm, peak):
+    """The smaller single-stream cases (B1 at 2^20, which fits in L2 and is
+    timed per launch after an L2 flush; B1 and Polar at 2^26), and the
+    4096-stream batched workload with every stream B1, every stream Polar, and
+    mixed, each as one graph launch in the configuration the step uses,
+    against a single stream of the same total length."""
+    import torch
+    nr = step.nr
+    dev = step.out_b1.device
+    out = {}
+    flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+    ws_small = nr.polar_workspace(1 << 26, dev)
+    cases = {
+        "c1_b1_accurate_2p20": (1 << 20, lambda b: nr.nrng_boxmuller(b, 0.0, 1.0, KEY, step.base, "accurate")),
+        "c2_b1_accurate_2p26": (1 << 26, lambda b: nr.nrng_boxmuller(b, 0.0, 1.0, KEY, step.base, "accurate")),
+        "c2_polar_accurate_2p26": (1 << 26, lambda b: nr.nrng_polar(b, 0.0, 1.0, KEY, step.base, ws_small,
+                                                                    "accurate")),
+    }
+    for name, (n, call) in cases.items():
+        buf = step.out_b1[:n]
+        for _ in range(warm):
+            call(buf)
+        check_ws(nr, ws_small)
+        if n * 4 < (129 << 20):
+            ms, stats = timed_flushed(lambda: call(buf), K, flush_buf.zero_)
+        else:
+            ms, stats = timed_launches(lambda: call(buf), K)
+        check_ws(nr, ws_small)
+        gbs = n * 4 / (ms * 1e-3) / 1e9
+        out[name] = {"n": n, "ms": round(ms, 4), "normals_per_s": n / (ms * 1e-3), "GB_per_s": round(gbs, 1),
+                     "frac_of_hbm": round(gbs / peak, 4), **stats}
+    del flush_buf
+    for methods in ("b1", "polar", "mixed"):
+        wl = step.W.batched_workload(methods=methods, align=4)
+        desc = nr.stream_descriptors(wl.offset, wl.n, wl.mu, wl.sigma, wl.key, wl.counter + np.uint64(step.base),
+                                     wl.method)
+        normals = int(wl.n.sum())
+        buf = torch.empty(wl.total, dtype=torch.float32, device=dev)
+        ws = torch.empty(nr.nrng_batched_workspace_size(desc), dtype=torch.uint8, device=dev)
+        dd = nr.descriptors_to_device(desc, dev)
+        g = nr.BatchedGraph(buf, dd, len(desc), ws, "accurate")
+        for _ in range(warm):
+            g.launch()
+        check_ws(nr, ws)
+        ms, stats = timed_launches(g.launch, K)
+        check_ws(nr, ws)
+        g.close()
+        gbs = normals * 4 / (ms * 1e-3) / 1e9
+        entry = {"streams": len(desc), "normals": normals, "ms": round(ms, 4), "normals_per_s": normals / (ms * 1e-3),
+                 "GB_per_s": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4), **stats}
+        if methods != "mixed":
+            one = buf[:normals]
+            ws_one = nr.polar_workspace(normals, dev) if methods == "polar" else None
+            if methods == "b1":
+                def single():
+                    nr.nrng_boxmuller(one, 0.0, 1.0, KEY, step.base, "accurate")
+            else:
+                def single():
+                    nr.nrng_polar(one, 0.0, 1.0, KEY, step.base, ws_one, "accurate")
+            for _ in range(warm):
+                single()
+            ms1, _ = timed_launches(single, K)
+            if ws_one is not None:
+                check_ws(nr, ws_one)
+            entry["single_stream_ms"] = round(ms1, 4)
+            entry["single_stream_over_batched"] = round(ms1 / ms, 4)
+        out[f"batched_{methods}"] = entry
+        del buf, ws, dd
+    step.check_status()
+    return out
+
+
 # ------------------------------------------------------------------- arms --
 def bench_reference(args):
     rank, world, _ = dist_env()
@@ -729,6 +817,7 @@ def bench_ours(args):
     ceiling = None
     if not args.no_sweep:
         sweep = precision_sweep(step, K, args.warmup, peak)
+        sweep.update(configs_sweep(step, K, args.warmup, peak))
         ceiling = write_ceiling(step.out_b1, K, args.warmup)
 
     cpu = None

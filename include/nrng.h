@@ -28,6 +28,12 @@
  * enqueueing its work.  Calls that take a workspace may not overlap on the
  * GPU with another call using the same workspace.
  *
+ * Threads.  Every call may be made from several host threads at once, each
+ * with its own buffers and workspaces (on its own streams, or ordered on a
+ * shared one).  The process-wide state (cached occupancies and SM counts,
+ * the batched configuration table and its autotune cache file, the
+ * no-workspace Polar call's device array) is guarded by atomics or a mutex.
+ *
  * Errors.  Every call returns an nrng_status_t.  Errors the host can detect
  * (a null pointer with n > 0, n < 0, sigma < 0 or not finite, mu not finite,
  * an unknown enum, a misaligned pointer, a workspace that is too small, a

@@ -382,13 +382,10 @@ k_batched(BatchedParams bp)
 template <int THREADS, int BPT, int MODE, typename T>
 static cudaError_t batched_main(const BatchedParams &bp, cudaStream_t s)
 {
-    static int occ = 0;
-    if (occ == 0) {
-        int o = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batched<THREADS, BPT, MODE, T>, THREADS, 0);
-        if (e != cudaSuccess) return e;
-        occ = std::max(o, 1);
-    }
+    static std::atomic<int> slot{0};
+    int occ = 0;
+    const cudaError_t e = cached_occupancy(slot, k_batched<THREADS, BPT, MODE, T>, THREADS, occ);
+    if (e != cudaSuccess) return e;
     k_batched<THREADS, BPT, MODE, T><<<sm_count() * occ, THREADS, 0, s>>>(bp);
     return cudaGetLastError();
 }

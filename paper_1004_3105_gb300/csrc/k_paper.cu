@@ -66,15 +66,11 @@ cudaError_t launch_b3(void *out, int64_t n, float mu, float sigma, uint64_t key,
 template <class Policy, int OCC_THREADS, typename T>
 static cudaError_t reject_launch_t(const PolarParams &p, bool aligned, cudaStream_t s)
 {
-    static int occ_a = 0, occ_p = 0;
-    int &occ = aligned ? occ_a : occ_p;
+    static std::atomic<int> occ_a{0}, occ_p{0};
     auto kern = aligned ? k_reject<Policy, OCC_THREADS, T, true> : k_reject<Policy, OCC_THREADS, T, false>;
-    if (occ == 0) {
-        int o = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kPolarThreads, 0);
-        if (e != cudaSuccess) return e;
-        occ = std::max(o, 1);
-    }
+    int occ = 0;
+    const cudaError_t e = cached_occupancy(aligned ? occ_a : occ_p, kern, kPolarThreads, occ);
+    if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>((int64_t)sm_count() * occ, p.tiles_max);
     kern<<<(int)grid, kPolarThreads, 0, s>>>(p);
     return cudaGetLastError();

@@ -33,15 +33,11 @@ size_t polar_workspace_bytes(int64_t n)
 template <int MODE, typename T>
 static cudaError_t polar_launch_t(const PolarParams &p, bool aligned, cudaStream_t s)
 {
-    static int occ_aligned = 0, occ_plain = 0;
-    int &occ = aligned ? occ_aligned : occ_plain;
+    static std::atomic<int> occ_aligned{0}, occ_plain{0};
     auto kern = aligned ? k_reject<PolarPolicy<MODE>, 1536, T, true> : k_reject<PolarPolicy<MODE>, 1536, T, false>;
-    if (occ == 0) {
-        int o = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kPolarThreads, 0);
-        if (e != cudaSuccess) return e;
-        occ = std::max(o, 1);
-    }
+    int occ = 0;
+    const cudaError_t e = cached_occupancy(aligned ? occ_aligned : occ_plain, kern, kPolarThreads, occ);
+    if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>((int64_t)sm_count() * occ, p.tiles_max);
     kern<<<(int)grid, kPolarThreads, 0, s>>>(p);
     return cudaGetLastError();
@@ -190,15 +186,11 @@ static cudaError_t polar_twopass_t(const PolarParams &p, bool aligned, cudaStrea
     k_polar_scan<<<1, kScanThreads, 0, s>>>(counts, prefix, p.tiles_max, p.nitems, p.hdr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    static int occ_a = 0, occ_p = 0;
-    int &occ = aligned ? occ_a : occ_p;
+    static std::atomic<int> occ_a{0}, occ_p{0};
     auto kern = aligned ? k_polar_write<MODE, T, true> : k_polar_write<MODE, T, false>;
-    if (occ == 0) {
-        int o = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kPolarThreads, 0);
-        if (e != cudaSuccess) return e;
-        occ = std::max(o, 1);
-    }
+    int occ = 0;
+    e = cached_occupancy(aligned ? occ_a : occ_p, kern, kPolarThreads, occ);
+    if (e != cudaSuccess) return e;
     // tiles beyond the crossing one are skipped, so size the grid to the
     // expected number of tiles, not the budget
     const int64_t expect = (p.nitems * 100) / ((int64_t)kPolarCandPerTile * 78) + 2;

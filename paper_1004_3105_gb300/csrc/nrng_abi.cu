@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <climits>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -69,15 +70,17 @@ RoundKeys round_keys(uint64_t key)
 
 int sm_count()
 {
-    static int cached[64] = {0};
+    // per device; relaxed atomics, since concurrent first calls store the same value
+    static std::atomic<int> cached[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
-    if (cached[dev] == 0) {
-        int v = 0;
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        cached[dev] = v > 0 ? v : 148;
+        v = v > 0 ? v : 148;
+        cached[dev].store(v, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return v;
 }
 
 unsigned long long spin_limit_ns()

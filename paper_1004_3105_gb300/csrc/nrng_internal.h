@@ -2,6 +2,8 @@
 // kernels: launch parameter blocks, workspace layouts and launchers.
 #pragma once
 
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
@@ -180,5 +182,23 @@ int64_t debug_polar_tiles();
 // Device properties cached per device.
 int sm_count();
 unsigned long long spin_limit_ns();
+
+// Resident CTAs per SM of kernel `kern` at `threads` threads, computed on the
+// first call and kept in `slot` (one per kernel instantiation and process).
+// Host threads may call concurrently: the slot is a relaxed atomic, and
+// concurrent first calls store the same value.
+template <typename Kernel>
+cudaError_t cached_occupancy(std::atomic<int> &slot, Kernel kern, int threads, int &occ)
+{
+    int o = slot.load(std::memory_order_relaxed);
+    if (o == 0) {
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, threads, 0);
+        if (e != cudaSuccess) return e;
+        o = std::max(o, 1);
+        slot.store(o, std::memory_order_relaxed);
+    }
+    occ = o;
+    return cudaSuccess;
+}
 
 }  // namespace nrng

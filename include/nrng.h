@@ -32,7 +32,9 @@
  * with its own buffers and workspaces (on its own streams, or ordered on a
  * shared one).  The process-wide state (cached occupancies and SM counts,
  * the batched configuration table and its autotune cache file, the
- * no-workspace Polar call's device array) is guarded by atomics or a mutex.
+ * no-workspace Polar call's address lookup) is guarded by atomics or a
+ * mutex.  nrng_polar_noalloc's device array itself is shared by every call
+ * on a device: such calls must be ordered on the GPU (see that call).
  *
  * Errors.  Every call returns an nrng_status_t.  Errors the host can detect
  * (a null pointer with n > 0, n < 0, sigma < 0 or not finite, mu not finite,

@@ -74,9 +74,9 @@ typedef enum { NRNG_F32 = 0, NRNG_BF16 = 1, NRNG_F16 = 2 } nrng_dtype_t;
 
 /* NRNG_ACCURATE: for B1, ln(1 - u) and sin/cos(2 pi v) from the exact
  *   24-bit lattice integers (an exact split of 1 - u into 2^e f with the
- *   atanh series for ln f; an exact quarter-turn reduction of the angle with
- *   Taylor polynomials of the remainder), within 3e-7 relative and 1e-7
- *   absolute over the whole lattice; for P, CUDA's logf of s held as an exact
+ *   atanh series for ln f; angle addition from a table of 256 angles with
+ *   short Taylor polynomials of the exact remainder), within 3e-7 relative
+ *   and 1e-7 absolute over the whole lattice; for P, CUDA's logf of s held as an exact
  *   double-float.  Square roots and reciprocals by the hardware
  *   approximations, whose relative error (below 2^-22) moves a result by
  *   under 2e-7 of itself.  Error within 4e-6 max(1, |z|) of the FP64

@@ -227,13 +227,17 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
 }
 
 // ------------------------------------------------------------ main --------
-// The batched kernel carries both tile bodies (B1 and Polar), so it is
-// compiled for fewer resident threads than the single-stream Polar kernel
-// (1024 per SM, 64 registers a thread).
-template <int THREADS, int MODE>
+// The batched kernel carries both tile bodies (B1 and Polar) and per-stream
+// round keys, so it is compiled for at most 1024 resident threads per SM, and
+// for fewer where its tile's shared memory (with the 1 KB the runtime keeps
+// per CTA) admits fewer CTAs: the register budget follows from the smaller
+// count (128 x 16: six CTAs, up to 80 registers a thread; 128 x 12: eight, 64).
+template <int THREADS, int BPT, int MODE>
 struct BatchedOccupancy {
-    static constexpr int kThreads = 1024;
-    static constexpr int kMinBlocks = (kThreads / THREADS) > 0 ? (kThreads / THREADS) : 1;
+    static constexpr int kSmemBlocks = (228 * 1024) / ((int)sizeof(PolarSmem<THREADS, BPT>) + 1024 + 256);
+    static constexpr int kThreadBlocks = 1024 / THREADS;
+    static constexpr int kMin = kSmemBlocks < kThreadBlocks ? kSmemBlocks : kThreadBlocks;
+    static constexpr int kMinBlocks = kMin > 0 ? kMin : 1;
 };
 
 // One unit of work of a CTA: tiles [t0, t1) of stream `stream` (-1: none left).
@@ -302,7 +306,7 @@ __device__ __forceinline__ void batched_claim(const BatchedParams &bp, unsigned 
 }
 
 template <int THREADS, int BPT, int MODE, typename T>
-__global__ void __launch_bounds__(THREADS, (BatchedOccupancy<THREADS, MODE>::kMinBlocks))
+__global__ void __launch_bounds__(THREADS, (BatchedOccupancy<THREADS, BPT, MODE>::kMinBlocks))
 k_batched(BatchedParams bp)
 {
     constexpr int kCand = 2 * THREADS * BPT;

@@ -67,7 +67,7 @@ typedef enum {
     NRNG_ERR_CUDA = 5,            /* a CUDA runtime call or launch failed */
     NRNG_ERR_TIMEOUT = 6,         /* device: a look-back wait ran out */
     NRNG_ERR_EXHAUSTED = 7,       /* device: Polar needed more tiles than sized */
-    NRNG_ERR_NOT_SUPPORTED = 8    /* valid request this build does not handle */
+    NRNG_ERR_NOT_SUPPORTED = 8    /* a valid request this library version does not handle */
 } nrng_status_t;
 
 typedef enum { NRNG_F32 = 0, NRNG_BF16 = 1, NRNG_F16 = 2 } nrng_dtype_t;

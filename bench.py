@@ -681,33 +681,48 @@ def configs_sweep(step, K, warm, peak):
 
 
 # ------------------------------------------------------------------- arms --
+def workload_config(world, batch_total, rep_shape):
+    """The `config` object of both arms' JSON lines: the step's workload."""
+    return {"workload": "B1 2^28 fp32 + Polar 2^28 fp32 (accurate, mu 0, sigma 1, key 0x5EED0001) + "
+                        "4096 batched streams (seed 7, mixed, graph) + reparam fwd+bwd [1024, 8192]",
+            "N": N_FULL, "batched_normals": int(batch_total), "reparam_shape": list(rep_shape),
+            "l2": "every output > L2 (1 GiB per single-stream kernel); no flush",
+            "parallelism": f"replicas x{world}"}
+
+
 def bench_reference(args):
+    """The FP64 oracle, as it stands, on every host core: each step is a
+    bounded sample of the step's mix (B1 and Polar at 2^20 each, a 64-stream
+    slice of the batched workload and a [64, 8192] slice of the reparameterised
+    sample, per worker, at disjoint counters)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
+    from paper_1004_3105_gb300 import workloads as W
     oracle.build()
     n = 1 << 20
     pool = OraclePool()
     for _ in range(args.warmup):
-        pool.run(n, 1, False)
+        pool.run(n, 1, True)
     total, dt = 0, 0.0
     for _ in range(args.steps):
-        normals, t = pool.run(n, 1, False)
+        normals, t = pool.run(n, 1, True)
         total += normals
         dt += t
     pool.close()
     value = total / dt
     per_step = total // max(1, args.steps)
+    sample = (f"per step and worker: B1 2^20 + Polar 2^20 + 64 batched streams + reparam fwd+bwd [64, 8192] "
+              f"(FP64 C oracle, {pool.workers} workers, disjoint counters); {per_step} normals per step")
+    wl = W.batched_workload(methods="mixed", align=4)
     line = {
         "impl": "reference", "metric": "normals/s", "value": value, "unit": "normals/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"B1 + Polar normals, 2^20 each per worker per step on {pool.workers} host cores "
-                               f"(FP64 oracle), key 0x5EED0001",
-                   "sample_per_step": per_step},
+        "config": workload_config(args.gpus, wl.total, W.REPARAM_SHAPE),
         "cpu_baseline": {"value": value, "unit": "normals/s", "cores": pool.workers, "kind": "oracle",
-                         "sample": f"B1 2^20 + Polar 2^20 per worker per step, {args.steps} steps"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "normals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -830,11 +845,7 @@ def bench_ours(args):
             "metric": "normals/s", "value": value, "unit": "normals/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (Philox4x32-10 streams; seeded PCG64 inputs)",
-            "config": {"workload": "B1 2^28 fp32 + Polar 2^28 fp32 (accurate, mu 0, sigma 1, key 0x5EED0001) + "
-                                   "4096 batched streams (seed 7, mixed, graph) + reparam fwd+bwd [1024, 8192]",
-                       "N": N_FULL, "batched_normals": step.batch_total, "reparam_shape": list(step.rep_shape),
-                       "l2": "every output > L2 (1 GiB per single-stream kernel); no flush",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(world, step.batch_total, step.rep_shape),
             "parts": parts, "sweep": sweep, "write_ceiling": ceiling, "roofline": roofline,
             "roofline_philox": roofline_philox,
             "clocks": clocks.summary(),

@@ -89,9 +89,10 @@ def measured_peaks():
 # The sources each recorded kernel is compiled from (its translation unit and
 # the headers it includes).
 KERNEL_SOURCES = {
-    "k_b1": ["k_b1.cu", "nrng_device.cuh", "nrng_internal.h", "h_poly.inc"],
-    "k_polar": ["k_polar.cu", "tiles.cuh", "nrng_device.cuh", "nrng_internal.h", "h_poly.inc"],
-    "k_batched": ["k_batched.cu", "tiles.cuh", "nrng_device.cuh", "nrng_internal.h", "h_poly.inc"],
+    "k_b1": ["k_b1.cu", "nrng_device.cuh", "nrng_internal.h", "h_poly.inc", "sincos_table.inc"],
+    "k_polar": ["k_polar.cu", "tiles.cuh", "nrng_device.cuh", "nrng_internal.h", "h_poly.inc", "sincos_table.inc"],
+    "k_batched": ["k_batched.cu", "tiles.cuh", "nrng_device.cuh", "nrng_internal.h", "h_poly.inc",
+                  "sincos_table.inc"],
 }
 
 

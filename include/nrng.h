@@ -37,7 +37,8 @@
  * on a device: such calls must be ordered on the GPU (see that call).
  *
  * Errors.  Every call returns an nrng_status_t.  Errors the host can detect
- * (a null pointer with n > 0, n < 0, sigma < 0 or not finite, mu not finite,
+ * (a null pointer with n > 0, n < 0, n above 2^60, or above 2^48 for the
+ * rejection methods, sigma < 0 or not finite, mu not finite,
  * an unknown enum, a misaligned pointer, a workspace that is too small, a
  * Philox counter that would pass 2^64) return at once and enqueue nothing.
  * A failed launch returns NRNG_ERR_CUDA.  Errors only the device can see

@@ -106,6 +106,10 @@ int64_t debug_polar_tiles()
 }
 
 static bool finite_f(float v) { return std::isfinite(v); }
+// Largest element (or point) count a call takes: far above any device
+// memory, and low enough that no size arithmetic on it can overflow int64.
+constexpr int64_t kMaxElements = int64_t(1) << 60;
+
 static bool valid_dtype(int32_t d) { return d == NRNG_F32 || d == NRNG_BF16 || d == NRNG_F16; }
 static bool valid_mode(int32_t m) { return m == NRNG_ACCURATE || m == NRNG_FAST; }
 static size_t dtype_size(int32_t d) { return d == NRNG_F32 ? 4 : 2; }
@@ -226,7 +230,7 @@ int32_t nrng_abi_version(void) { return 1; }
 int32_t nrng_uniform(float *d_out, int64_t n, uint64_t key, uint64_t counter, nrng_stream_t stream)
 {
     const CallRange range("nrng_uniform");
-    if (n < 0 || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
+    if (n < 0 || n > kMaxElements || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if ((uintptr_t)d_out % 4) return NRNG_ERR_MISALIGNED;
     if (n == 0) return NRNG_OK;
     if (!counter_fits(counter, (uint64_t)((n + 3) / 4))) return NRNG_ERR_COUNTER_OVERFLOW;
@@ -237,7 +241,7 @@ int32_t nrng_boxmuller(void *d_out, int64_t n, float mu, float sigma, uint64_t k
                        int32_t dtype, int32_t mode, nrng_stream_t stream)
 {
     const CallRange range("nrng_boxmuller");
-    if (n < 0 || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
+    if (n < 0 || n > kMaxElements || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if (!valid_dtype(dtype) || !(valid_mode(mode) || mode == NRNG_B2)) return NRNG_ERR_INVALID_VALUE;
     if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
     if ((uintptr_t)d_out % dtype_size(dtype)) return NRNG_ERR_MISALIGNED;
@@ -352,7 +356,7 @@ int32_t nrng_boxmuller_b3(void *d_out, int64_t n, float mu, float sigma, uint64_
                           int32_t dtype, nrng_stream_t stream)
 {
     const CallRange range("nrng_boxmuller_b3");
-    if (n < 0 || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
+    if (n < 0 || n > kMaxElements || (n > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if (!valid_dtype(dtype)) return NRNG_ERR_INVALID_VALUE;
     if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
     if ((uintptr_t)d_out % dtype_size(dtype)) return NRNG_ERR_MISALIGNED;
@@ -450,7 +454,7 @@ int32_t nrng_eval_points(int32_t kind, int32_t mode, const void *d_in, int64_t n
     const CallRange range("nrng_eval_points");
     if (kind < NRNG_POINTS_B1 || kind > NRNG_POINTS_B3) return NRNG_ERR_INVALID_VALUE;
     if (!(valid_mode(mode) || (mode == NRNG_B2 && kind == NRNG_POINTS_B1))) return NRNG_ERR_INVALID_VALUE;
-    if (n < 0 || (n > 0 && (d_in == nullptr || d_out == nullptr))) return NRNG_ERR_INVALID_VALUE;
+    if (n < 0 || n > kMaxElements || (n > 0 && (d_in == nullptr || d_out == nullptr))) return NRNG_ERR_INVALID_VALUE;
     if (!finite_f(mu) || !finite_f(sigma) || sigma < 0.0f) return NRNG_ERR_INVALID_VALUE;
     if ((uintptr_t)d_in % 4 || (uintptr_t)d_out % 4 || (uintptr_t)d_accept % 4) return NRNG_ERR_MISALIGNED;
     if (n == 0) return NRNG_OK;
@@ -492,7 +496,7 @@ int32_t nrng_reparam_fwd(float *d_x, const float *d_mu, const float *d_sigma, in
                          int64_t inner, uint64_t key, uint64_t counter, int32_t mode, nrng_stream_t stream)
 {
     const CallRange range("nrng_reparam_fwd");
-    if (n < 0 || m < 1 || inner < 1 || !valid_mode(mode)) return NRNG_ERR_INVALID_VALUE;
+    if (n < 0 || n > kMaxElements || m < 1 || inner < 1 || !valid_mode(mode)) return NRNG_ERR_INVALID_VALUE;
     if (n > 0 && (d_x == nullptr || d_mu == nullptr || d_sigma == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if (m > INT64_MAX / inner || n % (m * inner) != 0) return NRNG_ERR_INVALID_VALUE;
     if ((uintptr_t)d_x % 4 || (uintptr_t)d_mu % 4 || (uintptr_t)d_sigma % 4) return NRNG_ERR_MISALIGNED;
@@ -506,7 +510,7 @@ int32_t nrng_reparam_bwd(float *d_dmu, float *d_dsigma, const float *d_g, int64_
                          uint64_t key, uint64_t counter, int32_t mode, nrng_stream_t stream)
 {
     const CallRange range("nrng_reparam_bwd");
-    if (n < 0 || m < 1 || inner < 1 || !valid_mode(mode)) return NRNG_ERR_INVALID_VALUE;
+    if (n < 0 || n > kMaxElements || m < 1 || inner < 1 || !valid_mode(mode)) return NRNG_ERR_INVALID_VALUE;
     if (n > 0 && (d_dsigma == nullptr || d_g == nullptr)) return NRNG_ERR_INVALID_VALUE;
     if (m > INT64_MAX / inner || n % (m * inner) != 0) return NRNG_ERR_INVALID_VALUE;
     if ((uintptr_t)d_dmu % 4 || (uintptr_t)d_dsigma % 4 || (uintptr_t)d_g % 4) return NRNG_ERR_MISALIGNED;

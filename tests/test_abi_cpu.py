@@ -178,6 +178,20 @@ def test_batched_workspace_size(lib):
     assert f(FAKE, FAKE, 0, 0, 0, FAKE, 16, None) == _lib.OK
 
 
+def test_element_counts_above_2p60_rejected(lib):
+    """Counts beyond 2^60 (where the size arithmetic could overflow int64)
+    are rejected before anything is enqueued, up to INT64_MAX."""
+    for n in (2 ** 60 + 1, 2 ** 63 - 1):
+        assert lib.nrng_uniform(FAKE, n, 1, 0, None) == _lib.ERR_INVALID_VALUE
+        assert lib.nrng_boxmuller(FAKE, n, 0.0, 1.0, 1, 0, 0, 0, None) == _lib.ERR_INVALID_VALUE
+        assert lib.nrng_boxmuller_b3(FAKE, n, 0.0, 1.0, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE
+        assert lib.nrng_eval_points(0, 0, FAKE, n, 0.0, 1.0, FAKE, None, None) == _lib.ERR_INVALID_VALUE
+        assert lib.nrng_reparam_fwd(FAKE, FAKE, FAKE, n, 1, 1, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE
+        assert lib.nrng_reparam_bwd(FAKE, FAKE, FAKE, n, 1, 1, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE
+    # at the cap the host checks pass on to the counter check
+    assert lib.nrng_uniform(FAKE, 2 ** 60, 1, 2 ** 64 - 1, None) == _lib.ERR_COUNTER_OVERFLOW
+
+
 def test_reparam_validation(lib):
     f = lib.nrng_reparam_fwd
     assert f(FAKE, FAKE, FAKE, 12, 5, 1, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE     # 5 does not divide 12

@@ -287,7 +287,8 @@ int32_t nrng_polar_noalloc(void *d_out, int64_t n, float mu, float sigma, uint64
                            int32_t *d_status, nrng_stream_t stream);
 
 /* Workspace bytes nrng_batched needs for the k streams described in h_desc
- * (host copy of the descriptors).  Pure host computation. */
+ * (host copy of the descriptors).  Pure host computation.  A descriptor with
+ * n above 2^60 returns NRNG_ERR_INVALID_VALUE. */
 int32_t nrng_batched_workspace_size(const nrng_stream_desc_t *h_desc, int32_t k,
                                     size_t *h_bytes);
 

@@ -466,6 +466,8 @@ int32_t nrng_eval_points(int32_t kind, int32_t mode, const void *d_in, int64_t n
 int32_t nrng_batched_workspace_size(const nrng_stream_desc_t *h_desc, int32_t k, size_t *h_bytes)
 {
     if (h_bytes == nullptr || k < 0 || (k > 0 && h_desc == nullptr)) return NRNG_ERR_INVALID_VALUE;
+    for (int32_t j = 0; j < k; ++j)
+        if (h_desc[j].n > kMaxElements) return NRNG_ERR_INVALID_VALUE;
     *h_bytes = batched_workspace_bytes(h_desc, k);
     return NRNG_OK;
 }

@@ -170,6 +170,9 @@ def test_batched_workspace_size(lib):
             s += (need * 100 + cand * 78 - 1) // (cand * 78) + 1
         worst = max(worst, s)
     assert b.value == fixed + 8 * worst
+    big = _desc([100, 2 ** 60 + 1], [0, 0])   # a stream beyond the element cap
+    assert lib.nrng_batched_workspace_size(big.ctypes.data_as(ctypes.c_void_p), len(big),
+                                           ctypes.byref(b)) == _lib.ERR_INVALID_VALUE
     f = lib.nrng_batched
     assert f(FAKE, FAKE, -1, 0, 0, FAKE, 1 << 20, None) == _lib.ERR_INVALID_VALUE
     assert f(FAKE, FAKE, 4, 0, 0, None, 1 << 20, None) == _lib.ERR_WORKSPACE

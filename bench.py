@@ -687,7 +687,8 @@ def workload_config(world, batch_total, rep_shape):
     return {"workload": "B1 2^28 fp32 + Polar 2^28 fp32 (accurate, mu 0, sigma 1, key 0x5EED0001) + "
                         "4096 batched streams (seed 7, mixed, graph) + reparam fwd+bwd [1024, 8192]",
             "N": N_FULL, "batched_normals": int(batch_total), "reparam_shape": list(rep_shape),
-            "l2": "every output > L2 (1 GiB per single-stream kernel); no flush",
+            "l2": "outputs > L2 (1 GiB per single-stream kernel, 1.8 GB batched); the reparam part's 32 MiB "
+                  "arrays are evicted by the 3.7 GB the other parts write each step; no flush",
             "parallelism": f"replicas x{world}"}
 
 

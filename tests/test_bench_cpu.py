@@ -41,3 +41,12 @@ def test_reference_arm_json_line():
 def test_reference_arm_other_ranks_print_nothing():
     out = run_reference({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert out.strip() == ""
+
+
+def test_source_digest_ignores_comments_and_tracks_code():
+    a = "int f(int x) {\n    return x + 1;   // one more\n}\n/* block\n comment */\n"
+    b = "int f(int x){return x+1;}"
+    c = "int f(int x) { return x + 2; }"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
+

@@ -74,6 +74,7 @@ def _load():
         "orc_polar_accept_points": (None, [P, P, P, i64]),
         "orc_polar_at": (None, [P, P, i64, f64, f64, u64, u64]),
         "orc_lattice_accept_count": (i64, []),
+        "orc_lattice_accept_count_h": (i64, [i64]),
         "orc_batched": (None, [P, i32, P, P, P, P, P, P, P]),
         "orc_b3": (None, [P, i64, f64, f64, u64, u64]),
         "orc_b3_points": (None, [P, P, P, P, i64, f64, f64]),
@@ -195,8 +196,12 @@ def polar_at(cand, mu: float, sigma: float, key: int, counter: int) -> np.ndarra
     return out
 
 
-def lattice_accept_count() -> int:
-    return int(_load().orc_lattice_accept_count())
+def lattice_accept_count(half_width: int = None) -> int:
+    """Accepted points of step 3 on the lattice of half-width H (default the
+    generator's 2^23): #{(a, b) in [-H, H)^2 : 0 < a^2 + b^2 < H^2}."""
+    if half_width is None:
+        return int(_load().orc_lattice_accept_count())
+    return int(_load().orc_lattice_accept_count_h(int(half_width)))
 
 
 def b3(n: int, mu: float, sigma: float, key: int, counter: int) -> np.ndarray:

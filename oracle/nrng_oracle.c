@@ -276,10 +276,12 @@ void orc_polar_at(double *out2, const int64_t *cand, int64_t m, double mu, doubl
     }
 }
 
-/* Exact number of accepted lattice points,
- *   A = #{(a, b) in [-2^23, 2^23)^2 : 0 < a^2 + b^2 < 2^46},
+/* Exact number of accepted lattice points of half-width H,
+ *   A(H) = #{(a, b) in [-H, H)^2 : 0 < a^2 + b^2 < H^2},
  * by brute force over a with an exact integer square root for the range of
- * b; the acceptance probability of step 3 is A / 2^48. */
+ * b.  The generator's lattice has H = 2^23 (x = a 2^-23 in [-1, 1)), and the
+ * acceptance probability of step 3 is A(2^23) / 2^48; smaller H give the same
+ * count on coarser lattices, so that it can be checked by enumeration. */
 static int64_t orc_isqrt(int64_t v) /* largest t >= 0 with t*t <= v, v >= 0 */
 {
     int64_t t = (int64_t)sqrt((double)v);
@@ -288,9 +290,9 @@ static int64_t orc_isqrt(int64_t v) /* largest t >= 0 with t*t <= v, v >= 0 */
     return t;
 }
 
-int64_t orc_lattice_accept_count(void)
+int64_t orc_lattice_accept_count_h(int64_t H)
 {
-    const int64_t H = (int64_t)1 << 23, R = (int64_t)1 << 46;
+    const int64_t R = H * H;
     int64_t total = 0;
     for (int64_t a = -H; a < H; ++a) {
         int64_t rem = R - a * a; /* need b^2 < rem, i.e. b^2 <= rem - 1 */
@@ -301,6 +303,11 @@ int64_t orc_lattice_accept_count(void)
         if (hi >= lo) total += hi - lo + 1;
     }
     return total - 1; /* the origin has s = 0 and is rejected */
+}
+
+int64_t orc_lattice_accept_count(void)
+{
+    return orc_lattice_accept_count_h((int64_t)1 << 23);
 }
 
 /* ------------------------------------------------------- Method B3 (Sec 3) */

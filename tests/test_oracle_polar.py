@@ -5,6 +5,7 @@ the closed forms of step 4, uniformity of s (Sec. 2), and normality."""
 import math
 
 import numpy as np
+import pytest
 
 import oracle
 from stats import check_standard_normal_moments, ks_critical, ks_distance, normal_cdf
@@ -19,6 +20,25 @@ def test_lattice_accept_count_is_pi_over_4():
     assert abs(a - math.pi * 2.0 ** 46) < 2 * math.pi * H
     # the count is even in each coordinate sign pattern except the axes: sanity of range
     assert 0.78 * 2 ** 48 < a < 0.79 * 2 ** 48
+
+
+@pytest.mark.parametrize("half_width", [1, 2, 3, 4, 5, 7, 8, 16, 31, 100, 181, 1024, 3000])
+def test_lattice_accept_count_equals_enumeration(half_width):
+    # exact pin of the count: every lattice point of half-width H enumerated,
+    # with the strict bound s < 1 (a^2 + b^2 = H^2 rejected, e.g. (-H, 0)) and
+    # the origin rejected (s = 0), as step 3 and the S = 0 reading fix them
+    a = np.arange(-half_width, half_width, dtype=np.int64)
+    s = a[:, None] * a[:, None] + a[None, :] * a[None, :]
+    want = int(np.count_nonzero((s > 0) & (s < half_width * half_width)))
+    assert oracle.lattice_accept_count(half_width) == want
+
+
+def test_lattice_accept_count_small_cases_by_hand():
+    # H = 1: only (-1,-1), (-1,0), (0,-1), (0,0); none has 0 < s < 1.
+    # H = 2: the eight neighbours of the origin with |a|,|b| <= 1 (s = 1 or 2 < 4);
+    # (-2, 0) and (0, -2) sit on the circle s = 4 and are rejected.
+    assert oracle.lattice_accept_count(1) == 0
+    assert oracle.lattice_accept_count(2) == 8
 
 
 def test_accept_bits_brute_force():

@@ -280,7 +280,10 @@ int32_t nrng_eval_points(int32_t kind, int32_t mode, const void *d_in, int64_t n
  * uses first, so calls ordered on the GPU are independent, but calls that
  * overlap on the GPU (unordered streams) race on it.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture. */
+ * that device current; make that first call before any stream capture.  The
+ * address is kept for the life of the process, which assumes one CUDA
+ * context per device: after cudaDeviceReset the call must not be used again
+ * in that process. */
 int32_t nrng_polar_noalloc(void *d_out, int64_t n, float mu, float sigma, uint64_t key,
                            uint64_t counter, int32_t dtype, int32_t mode,
                            uint64_t *d_next_counter, int64_t *d_pair_candidate,

@@ -24,7 +24,11 @@
 //   * the array's host-side name is only a stand-in for the device symbol: the
 //     device address is obtained once per device with cudaGetSymbolAddress,
 //     with that device current, by the first call on that device.  Make that
-//     first call before any stream capture that would include it.
+//     first call before any stream capture that would include it.  The cached
+//     address assumes one CUDA context per device for the life of the
+//     process: after cudaDeviceReset (or any teardown of the primary context)
+//     the cached address is stale, so do not call this entry point again in
+//     that process.
 #include <mutex>
 
 #include "nrng_internal.h"

@@ -118,6 +118,18 @@ int32_t nrng_abi_version(void);
 int32_t nrng_uniform(float *d_out, int64_t n, uint64_t key, uint64_t counter,
                      nrng_stream_t stream);
 
+/* Measurement aid: the uniform generator alone.  Draws the Philox blocks
+ * [counter, counter + nblocks) of `key` and stores the xor of all their words
+ * in *d_out (one uint32, device memory, 4-byte aligned), with no other
+ * stores, so that its time is this GPU's rate of drawing blocks: the
+ * instruction ceiling shared by every generator here.  The paper's Table 1
+ * counts uniform generation inside the "other" cycles of each method (Sec. 3);
+ * this call measures that share on its own.  nblocks <= 2^31 with a low
+ * counter word that does not wrap (counter mod 2^32 + nblocks <= 2^32),
+ * else NRNG_ERR_NOT_SUPPORTED. */
+int32_t nrng_philox_ceiling(uint32_t *d_out, int64_t nblocks, uint64_t key, uint64_t counter,
+                            nrng_stream_t stream);
+
 /* Box-Muller, Algorithm B1 (paper Sec. 2, steps 1-3, notes a and b).
  * Block b gives two pairs: (u, v) from words (w0, w1) and from (w2, w3).
  * For each, r = sigma sqrt(-2 ln(1 - u)), x = r sin(2 pi v) + mu,

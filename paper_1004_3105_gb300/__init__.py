@@ -12,6 +12,6 @@ from .nrng import (  # noqa: F401
     nrng_batched_get_config, nrng_batched_set_config, nrng_batched_workspace_size, nrng_boxmuller,
     nrng_boxmuller_b3, nrng_eval_points, nrng_get_status, nrng_polar, nrng_polar_max_blocks, nrng_polar_noalloc, nrng_polar_p2,
     nrng_polar_twopass, nrng_polar_twopass_workspace_size, nrng_polar_workspace_size, nrng_ratio,
-    nrng_ratio_workspace_size, nrng_reparam_bwd, nrng_reparam_fwd, nrng_uniform, polar_workspace,
+    nrng_ratio_workspace_size, nrng_reparam_bwd, nrng_reparam_fwd, nrng_uniform, nrng_philox_ceiling, polar_workspace,
     raise_on_status, ratio_workspace, stream_descriptors,
 )

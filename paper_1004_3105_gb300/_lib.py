@@ -42,6 +42,7 @@ SIGNATURES = {
     "nrng_status_string": (ctypes.c_char_p, [_I32]),
     "nrng_abi_version": (_I32, []),
     "nrng_uniform": (_I32, [_P, _I64, _U64, _U64, _P]),
+    "nrng_philox_ceiling": (_I32, [_P, _I64, _U64, _U64, _P]),
     "nrng_boxmuller": (_I32, [_P, _I64, _F32, _F32, _U64, _U64, _I32, _I32, _P]),
     "nrng_polar_workspace_size": (_I32, [_I64, _PSZ]),
     "nrng_polar_max_blocks": (_I32, [_I64, _PU64]),

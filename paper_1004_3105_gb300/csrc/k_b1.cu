@@ -2,9 +2,10 @@
 //
 // One thread takes one Philox block at a time (grid-stride): four 32-bit
 // words give two (u, v) pairs and four outputs, stored with one 16-byte
-// (fp32) or 8-byte (bf16/fp16) streaming store.  There are no loads: the
-// kernel is bound by the HBM write stream or by the Philox + transform
-// instruction issue, whichever is tighter.
+// (fp32) or 8-byte (bf16/fp16) streaming store.  The only loads are the
+// accurate path's 16 KB sin/cos table, copied to shared memory once per CTA.
+// The kernel is bound by the HBM write stream or by instruction dispatch
+// (Philox's 32x32->64 products and the transform), whichever is tighter.
 #include <algorithm>
 
 #include "nrng_device.cuh"
@@ -39,70 +40,91 @@ __global__ void __launch_bounds__(kB1Threads)
 k_b1(T *__restrict__ out, int64_t n, int64_t nblocks, float mu, float sigma, uint64_t counter,
      const RoundKeys rk)
 {
+    __shared__ float4 s_tab[MODE == kModeAccurate ? 1024 : 1];
+    const float4 *tab = b1_table_to_shared<MODE>(s_tab);
+    const B1Coef cf = b1_coef(mu, sigma);
     const int64_t stride = (int64_t)gridDim.x * kB1Threads;
     for (int64_t b = (int64_t)blockIdx.x * kB1Threads + threadIdx.x; b < nblocks; b += stride) {
-        const uint4 w = philox_block(counter + (uint64_t)b, rk);
-        float x0, y0, x1, y1;
-        b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
-        b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
+        const float4 o = b1_block<MODE>(philox_block(counter + (uint64_t)b, rk), cf, tab);
         const int64_t i = 4 * b;
         if (ALIGNED && i + 4 <= n) {
-            store4_aligned(out + i, x0, y0, x1, y1);
+            store4_aligned(out + i, o.x, o.y, o.z, o.w);
         } else {
-            if (i < n) store1(out + i, x0);
-            if (i + 1 < n) store1(out + i + 1, y0);
-            if (i + 2 < n) store1(out + i + 2, x1);
-            if (i + 3 < n) store1(out + i + 3, y1);
+            if (i < n) store1(out + i, o.x);
+            if (i + 1 < n) store1(out + i + 1, o.y);
+            if (i + 2 < n) store1(out + i + 2, o.z);
+            if (i + 3 < n) store1(out + i + 3, o.w);
         }
     }
 }
 
 // The common case: output aligned to 4 elements and fewer than 2^32 blocks.
-// The loop runs over whole blocks only, with 32-bit indices and the 64-bit
-// counter split into words; the last, partial block (n mod 4 outputs) is
-// done by one thread after it.
-template <int MODE, typename T>
+// The loop runs over whole blocks only, with 32-bit indices; the last,
+// partial block (n mod 4 outputs) is done by one thread after it.  With
+// CARRY false the low counter word does not wrap over the launch (c_lo plus
+// the blocks stays below 2^32), so the high word is the launch constant c_hi:
+// the first two Philox rounds then partly fold into launch constants.
+template <int MODE, typename T, bool CARRY>
 __global__ void __launch_bounds__(kB1Threads)
 k_b1_whole(T *__restrict__ out, int64_t n, uint32_t nwhole, float mu, float sigma, uint32_t c_lo,
            uint32_t c_hi, const RoundKeys rk)
 {
+    __shared__ float4 s_tab[MODE == kModeAccurate ? 1024 : 1];
+    const float4 *tab = b1_table_to_shared<MODE>(s_tab);
+    const B1Coef cf = b1_coef(mu, sigma);
     const uint32_t stride = gridDim.x * kB1Threads;
     // Two blocks per iteration (b and b + stride): their Philox chains are
-    // independent, so the integer-multiply and transform work of one fills
-    // the other's dependency stalls (measured: 4.8% faster fast path).
+    // independent, so one fills the other's dependency stalls.
     uint32_t b = blockIdx.x * kB1Threads + threadIdx.x;
     for (; b + stride < nwhole; b += 2 * stride) {
         const uint32_t b2 = b + stride;
         const uint32_t lo = c_lo + b, lo2 = c_lo + b2;
-        const uint32_t hi = c_hi + (lo < b ? 1u : 0u), hi2 = c_hi + (lo2 < b2 ? 1u : 0u);
-        const uint4 w = philox4x32_10(lo, hi, rk);
-        const uint4 w2 = philox4x32_10(lo2, hi2, rk);
-        float x0, y0, x1, y1, x2, y2, x3, y3;
-        b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
-        b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
-        b1_pair<MODE>(w2.x, w2.y, mu, sigma, x2, y2);
-        b1_pair<MODE>(w2.z, w2.w, mu, sigma, x3, y3);
-        store4_aligned(out + 4 * (size_t)b, x0, y0, x1, y1);
-        store4_aligned(out + 4 * (size_t)b2, x2, y2, x3, y3);
+        const uint32_t hi = CARRY ? c_hi + (lo < b ? 1u : 0u) : c_hi;
+        const uint32_t hi2 = CARRY ? c_hi + (lo2 < b2 ? 1u : 0u) : c_hi;
+        const float4 o = b1_block<MODE>(philox4x32_10(lo, hi, rk), cf, tab);
+        const float4 o2 = b1_block<MODE>(philox4x32_10(lo2, hi2, rk), cf, tab);
+        store4_aligned(out + 4 * (size_t)b, o.x, o.y, o.z, o.w);
+        store4_aligned(out + 4 * (size_t)b2, o2.x, o2.y, o2.z, o2.w);
     }
     if (b < nwhole) {
         const uint32_t lo = c_lo + b;
-        const uint32_t hi = c_hi + (lo < b ? 1u : 0u);
-        const uint4 w = philox4x32_10(lo, hi, rk);
-        float x0, y0, x1, y1;
-        b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
-        b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
-        store4_aligned(out + 4 * (size_t)b, x0, y0, x1, y1);
+        const uint32_t hi = CARRY ? c_hi + (lo < b ? 1u : 0u) : c_hi;
+        const float4 o = b1_block<MODE>(philox4x32_10(lo, hi, rk), cf, tab);
+        store4_aligned(out + 4 * (size_t)b, o.x, o.y, o.z, o.w);
     }
     if ((n & 3) && blockIdx.x == 0 && threadIdx.x == 0) {
         const uint64_t c = ((uint64_t)c_hi << 32 | c_lo) + nwhole;
-        const uint4 w = philox_block(c, rk);
-        float v[4];
-        b1_pair<MODE>(w.x, w.y, mu, sigma, v[0], v[1]);
-        b1_pair<MODE>(w.z, w.w, mu, sigma, v[2], v[3]);
+        const float4 o = b1_block<MODE>(philox_block(c, rk), cf, tab);
+        const float v[4] = {o.x, o.y, o.z, o.w};
         const int64_t i = 4 * (int64_t)nwhole;
         for (int q = 0; q < 4 && i + q < n; ++q) store1(out + i + q, v[q]);
     }
+}
+
+// Philox4x32-10 alone: every block of [counter, counter + nblocks) drawn and
+// folded into one word by xor, with no stores but one atomic per warp.  Its
+// time is the rate at which this GPU draws Philox blocks, the instruction
+// ceiling of every generator here (Philox's twenty 32x32->64 products and
+// twenty three-input xors a block).  Two independent blocks per iteration, as
+// in the B1 kernel; the low counter word must not wrap over the launch.
+__global__ void __launch_bounds__(kB1Threads)
+k_philox_ceiling(uint32_t *__restrict__ out, uint32_t nblocks, uint32_t c_lo, uint32_t c_hi, const RoundKeys rk)
+{
+    const uint32_t stride = gridDim.x * kB1Threads;
+    uint32_t acc = 0;
+    uint32_t b = blockIdx.x * kB1Threads + threadIdx.x;
+    for (; b + stride < nblocks; b += 2 * stride) {
+        const uint4 w = philox4x32_10(c_lo + b, c_hi, rk);
+        const uint4 w2 = philox4x32_10(c_lo + b + stride, c_hi, rk);
+        acc ^= w.x ^ w.y ^ w.z ^ w.w ^ w2.x ^ w2.y ^ w2.z ^ w2.w;
+    }
+    if (b < nblocks) {
+        const uint4 w = philox4x32_10(c_lo + b, c_hi, rk);
+        acc ^= w.x ^ w.y ^ w.z ^ w.w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicXor(out, acc);
 }
 
 // Grid: enough CTAs to fill every SM at full occupancy, grid-striding over
@@ -112,6 +134,15 @@ static int b1_grid(int64_t nblocks)
     const int64_t ctas = (nblocks + kB1Threads - 1) / kB1Threads;
     const int64_t resident = (int64_t)sm_count() * (2048 / kB1Threads);
     return (int)std::max<int64_t>(1, std::min(ctas, resident));
+}
+
+cudaError_t launch_philox_ceiling(uint32_t *out, int64_t nblocks, uint64_t key, uint64_t counter, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_philox_ceiling<<<b1_grid(nblocks), kB1Threads, 0, s>>>(out, (uint32_t)nblocks, (uint32_t)counter,
+                                                            (uint32_t)(counter >> 32), round_keys(key));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_uniform(float *out, int64_t n, uint64_t key, uint64_t counter, cudaStream_t s)
@@ -132,9 +163,15 @@ static void b1_dispatch_aligned(void *out, int64_t n, int64_t nblocks, float mu,
 {
     const int grid = b1_grid(nblocks);
     const int64_t nwhole = n / 4;
-    if (aligned && nwhole < (int64_t(1) << 32) - 2 * (int64_t)grid * kB1Threads)
-        k_b1_whole<MODE, T><<<grid, kB1Threads, 0, s>>>((T *)out, n, (uint32_t)nwhole, mu, sigma,
-                                                         (uint32_t)counter, (uint32_t)(counter >> 32), rk);
+    // the carry-free form when the low counter word does not wrap over the
+    // launch (the whole blocks and the partial one)
+    const bool carry_free = (uint64_t)(uint32_t)counter + (uint64_t)nblocks <= (uint64_t(1) << 32);
+    if (aligned && nwhole < (int64_t(1) << 32) - 2 * (int64_t)grid * kB1Threads && carry_free)
+        k_b1_whole<MODE, T, false><<<grid, kB1Threads, 0, s>>>((T *)out, n, (uint32_t)nwhole, mu, sigma,
+                                                                (uint32_t)counter, (uint32_t)(counter >> 32), rk);
+    else if (aligned && nwhole < (int64_t(1) << 32) - 2 * (int64_t)grid * kB1Threads)
+        k_b1_whole<MODE, T, true><<<grid, kB1Threads, 0, s>>>((T *)out, n, (uint32_t)nwhole, mu, sigma,
+                                                               (uint32_t)counter, (uint32_t)(counter >> 32), rk);
     else if (aligned)
         k_b1<MODE, T, true><<<grid, kB1Threads, 0, s>>>((T *)out, n, nblocks, mu, sigma, counter, rk);
     else

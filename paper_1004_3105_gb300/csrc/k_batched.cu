@@ -335,12 +335,14 @@ k_batched(BatchedParams bp)
             if (overflow) {
                 // B1 streams have no overflow tiles
             } else if (((uintptr_t)out % (4 * sizeof(T))) == 0) {
+                const B1Coef cf = b1_coef(d.mu, d.sigma);
                 for (int q = 0; q < kB1TilesPerItem; ++q)
-                    b1_tile<THREADS, BPT, MODE, T, true>(out, d.n, d.mu, d.sigma, rk, d.counter,
+                    b1_tile<THREADS, BPT, MODE, T, true>(out, d.n, cf, kSinCos1024, rk, d.counter,
                                                          t0 * kB1TilesPerItem + q);
             } else {
+                const B1Coef cf = b1_coef(d.mu, d.sigma);
                 for (int q = 0; q < kB1TilesPerItem; ++q)
-                    b1_tile<THREADS, BPT, MODE, T, false>(out, d.n, d.mu, d.sigma, rk, d.counter,
+                    b1_tile<THREADS, BPT, MODE, T, false>(out, d.n, cf, kSinCos1024, rk, d.counter,
                                                           t0 * kB1TilesPerItem + q);
             }
         } else if (!(overflow && skip)) {

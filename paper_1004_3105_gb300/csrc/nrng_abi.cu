@@ -237,6 +237,19 @@ int32_t nrng_uniform(float *d_out, int64_t n, uint64_t key, uint64_t counter, nr
     return cuda_status(launch_uniform(d_out, n, key, counter, (cudaStream_t)stream), "nrng_uniform");
 }
 
+int32_t nrng_philox_ceiling(uint32_t *d_out, int64_t nblocks, uint64_t key, uint64_t counter, nrng_stream_t stream)
+{
+    const CallRange range("nrng_philox_ceiling");
+    if (nblocks < 0 || (nblocks > 0 && d_out == nullptr)) return NRNG_ERR_INVALID_VALUE;
+    if ((uintptr_t)d_out % 4) return NRNG_ERR_MISALIGNED;
+    if (nblocks == 0) return NRNG_OK;
+    // 32-bit block indices and a low counter word that does not wrap
+    if (nblocks > (int64_t(1) << 31) || (uint64_t)(uint32_t)counter + (uint64_t)nblocks > (uint64_t(1) << 32))
+        return NRNG_ERR_NOT_SUPPORTED;
+    return cuda_status(launch_philox_ceiling(d_out, nblocks, key, counter, (cudaStream_t)stream),
+                       "nrng_philox_ceiling");
+}
+
 int32_t nrng_boxmuller(void *d_out, int64_t n, float mu, float sigma, uint64_t key, uint64_t counter,
                        int32_t dtype, int32_t mode, nrng_stream_t stream)
 {

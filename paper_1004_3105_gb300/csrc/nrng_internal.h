@@ -106,6 +106,7 @@ size_t polar_twopass_workspace_bytes(int64_t n);
 
 // ------------------------------------------------------------- launchers --
 cudaError_t launch_uniform(float *out, int64_t n, uint64_t key, uint64_t counter, cudaStream_t s);
+cudaError_t launch_philox_ceiling(uint32_t *out, int64_t nblocks, uint64_t key, uint64_t counter, cudaStream_t s);
 cudaError_t launch_b1(void *out, int64_t n, float mu, float sigma, uint64_t key, uint64_t counter,
                       int dtype, int mode, bool aligned, cudaStream_t s);
 cudaError_t launch_polar(const PolarParams &p, int dtype, int mode, bool aligned, cudaStream_t s);

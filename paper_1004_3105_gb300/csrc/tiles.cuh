@@ -10,7 +10,7 @@ namespace nrng {
 // Blocks [t*TB, (t+1)*TB) of a stream, TB = THREADS * BPT; block b writes
 // out[4b .. 4b+3] (Algorithm B1, two pairs per block).
 template <int THREADS, int BPT, int MODE, typename T, bool ALIGNED, typename Key>
-__device__ __forceinline__ void b1_tile(T *__restrict__ out, int64_t n, float mu, float sigma,
+__device__ __forceinline__ void b1_tile(T *__restrict__ out, int64_t n, const B1Coef &cf, const float4 *tab,
                                         const Key &rk, uint64_t counter, int64_t t)
 {
     const int64_t nblocks = (n + 3) / 4;
@@ -20,32 +20,24 @@ __device__ __forceinline__ void b1_tile(T *__restrict__ out, int64_t n, float mu
         const int64_t b = t * (THREADS * BPT) + r * THREADS + threadIdx.x;
         const int64_t b2 = b + THREADS;
         if (b2 < nblocks && ALIGNED && 4 * b2 + 4 <= n) {
-            const uint4 w = philox_block(counter + (uint64_t)b, rk);
-            const uint4 w2 = philox_block(counter + (uint64_t)b2, rk);
-            float x0, y0, x1, y1, x2, y2, x3, y3;
-            b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
-            b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
-            b1_pair<MODE>(w2.x, w2.y, mu, sigma, x2, y2);
-            b1_pair<MODE>(w2.z, w2.w, mu, sigma, x3, y3);
-            store4_aligned(out + 4 * b, x0, y0, x1, y1);
-            store4_aligned(out + 4 * b2, x2, y2, x3, y3);
+            const float4 o = b1_block<MODE>(philox_block(counter + (uint64_t)b, rk), cf, tab);
+            const float4 o2 = b1_block<MODE>(philox_block(counter + (uint64_t)b2, rk), cf, tab);
+            store4_aligned(out + 4 * b, o.x, o.y, o.z, o.w);
+            store4_aligned(out + 4 * b2, o2.x, o2.y, o2.z, o2.w);
             continue;
         }
         for (int q = 0; q < 2; ++q) {
             const int64_t bq = b + q * THREADS;
             if (bq >= nblocks) return;
-            const uint4 w = philox_block(counter + (uint64_t)bq, rk);
-            float x0, y0, x1, y1;
-            b1_pair<MODE>(w.x, w.y, mu, sigma, x0, y0);
-            b1_pair<MODE>(w.z, w.w, mu, sigma, x1, y1);
+            const float4 o = b1_block<MODE>(philox_block(counter + (uint64_t)bq, rk), cf, tab);
             const int64_t i = 4 * bq;
             if (ALIGNED && i + 4 <= n) {
-                store4_aligned(out + i, x0, y0, x1, y1);
+                store4_aligned(out + i, o.x, o.y, o.z, o.w);
             } else {
-                if (i < n) store1(out + i, x0);
-                if (i + 1 < n) store1(out + i + 1, y0);
-                if (i + 2 < n) store1(out + i + 2, x1);
-                if (i + 3 < n) store1(out + i + 3, y1);
+                if (i < n) store1(out + i, o.x);
+                if (i + 1 < n) store1(out + i + 1, o.y);
+                if (i + 2 < n) store1(out + i + 2, o.z);
+                if (i + 3 < n) store1(out + i + 3, o.w);
             }
         }
     }

@@ -74,6 +74,16 @@ def nrng_uniform(out: torch.Tensor, key: int, counter: int, stream=None) -> None
           "nrng_uniform")
 
 
+def nrng_philox_ceiling(out: torch.Tensor, nblocks: int, key: int, counter: int, stream=None) -> None:
+    """Draws Philox blocks [counter, counter + nblocks) and stores the xor of
+    all their words in out[0] (int32 or uint32 tensor): a measurement of the
+    generator's rate with no output traffic."""
+    if out.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)) or out.numel() < 1:
+        raise TypeError("nrng_philox_ceiling writes one 32-bit word")
+    check(load().nrng_philox_ceiling(_dev(out, "out"), int(nblocks), _u64(key), _u64(counter), _stream(stream)),
+          "nrng_philox_ceiling")
+
+
 def nrng_boxmuller(out: torch.Tensor, mu: float, sigma: float, key: int, counter: int,
                    mode="accurate", stream=None) -> None:
     """Algorithm B1 into `out` (float32, bfloat16 or float16)."""

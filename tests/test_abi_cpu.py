@@ -195,6 +195,17 @@ def test_element_counts_above_2p60_rejected(lib):
     assert lib.nrng_uniform(FAKE, 2 ** 60, 1, 2 ** 64 - 1, None) == _lib.ERR_COUNTER_OVERFLOW
 
 
+def test_philox_ceiling_validation(lib):
+    f = lib.nrng_philox_ceiling
+    assert f(None, 16, 1, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(FAKE, -1, 1, 0, None) == _lib.ERR_INVALID_VALUE
+    assert f(ctypes.c_void_p(0x100002), 16, 1, 0, None) == _lib.ERR_MISALIGNED
+    assert f(FAKE, 0, 1, 0, None) == _lib.OK
+    # 32-bit indices only, and a low counter word that does not wrap
+    assert f(FAKE, 2 ** 31 + 1, 1, 0, None) == _lib.ERR_NOT_SUPPORTED
+    assert f(FAKE, 16, 1, 2 ** 32 - 8, None) == _lib.ERR_NOT_SUPPORTED
+
+
 def test_reparam_validation(lib):
     f = lib.nrng_reparam_fwd
     assert f(FAKE, FAKE, FAKE, 12, 5, 1, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE     # 5 does not divide 12

@@ -21,23 +21,45 @@ def read(name):
 
 
 def test_sincos_table_is_generated_and_accurate():
-    pairs = re.findall(r"\{(-?0x[0-9a-f.]+p[+-]\d+)f, (-?0x[0-9a-f.]+p[+-]\d+)f\}", read("sincos_table.inc"))
-    assert len(pairs) == 256
-    s = np.array([float.fromhex(a) for a, _ in pairs])
-    c = np.array([float.fromhex(b) for _, b in pairs])
-    gs, gc = gen_sincos_table.table()
-    np.testing.assert_array_equal(s, gs.astype(np.float64))
-    np.testing.assert_array_equal(c, gc.astype(np.float64))
-    # every entry is the float32 nearest to the true value: within half a float ulp
-    a = 2.0 * np.pi * np.arange(256) / 256.0
+    num = r"(-?0x[0-9a-f.]+p[+-]\d+)f"
+    rows = re.findall(r"\{" + ", ".join([num] * 4) + r"\}", read("sincos_table.inc"))
+    n = gen_sincos_table.N
+    assert len(rows) == n == 1024
+    t = np.array([[float.fromhex(x) for x in r] for r in rows])
+    s, c, hs, hc = t[:, 0], t[:, 1], t[:, 2], t[:, 3]
+    gs, gc, ghs, ghc = gen_sincos_table.table()
+    for got, want in ((s, gs), (c, gc), (hs, ghs), (hc, ghc)):
+        np.testing.assert_array_equal(got, want.astype(np.float64))
+    # every sin/cos entry is the float32 nearest to the true value: within half a float ulp
+    a = 2.0 * np.pi * np.arange(n) / n
     for got, ref in ((s, np.sin(a)), (c, np.cos(a))):
         half_ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64) / 2
         assert np.all(np.abs(got - ref) <= half_ulp + 1e-15)
         assert np.all(got.astype(np.float32) == got)
+    # the third and fourth columns are exact halvings, negated
+    np.testing.assert_array_equal(hs, -s / 2)
+    np.testing.assert_array_equal(hc, -c / 2)
     # exact at the quarter turns, and exactly quarter-turn symmetric
-    assert (s[0], c[0], s[64], c[64], s[128], c[128], s[192], c[192]) == (0, 1, 1, 0, 0, -1, -1, 0)
-    np.testing.assert_array_equal(s[64:], c[:192])
-    np.testing.assert_array_equal(c[64:], -s[:192])
+    q = n // 4
+    assert (s[0], c[0], s[q], c[q], s[2 * q], c[2 * q], s[3 * q], c[3 * q]) == (0, 1, 1, 0, 0, -1, -1, 0)
+    np.testing.assert_array_equal(s[q:], c[:3 * q])
+    np.testing.assert_array_equal(c[q:], -s[:3 * q])
+
+
+def test_sincos_angle_addition_error_bound():
+    # the quadratic angle addition the accurate B1 path evaluates, in float64
+    # from the float32 table over remainders delta in [0, 2 pi / 1024): its
+    # truncation (delta^3 / 6 and below) plus the table's rounding stays below
+    # 1e-7 of the true sin and cos, at every table angle
+    gs, gc, ghs, ghc = (x.astype(np.float64) for x in gen_sincos_table.table())
+    n = gen_sincos_table.N
+    d = np.linspace(0.0, 2.0 * np.pi / n, 257)[:-1]
+    i = np.arange(n)[:, None]
+    a = 2.0 * np.pi * i / n
+    s = gs[i] + d * (gc[i] + d * ghs[i])
+    c = gc[i] + d * (-gs[i] + d * ghc[i])
+    assert np.max(np.abs(s - np.sin(a + d))) < 1e-7
+    assert np.max(np.abs(c - np.cos(a + d))) < 1e-7
 
 
 def horner_f32(coef, v):

@@ -53,7 +53,11 @@ def test_b1_accurate_every_lattice_radius_and_angle():
     """The accurate B1 transform over its whole domain: every radius k (2^24
     values, at t = 0, where sin = 0 and cos = 1 exactly, so y = r) and every
     angle t (2^24 values, at u = 1 - e^-1/2, where r is near 1), against the
-    oracle.  r within 4e-7 of itself; x, y within 3e-7 absolute at r ~ 1."""
+    oracle.  The radius takes the hardware log2 of the exact 1 - u above
+    u = 1/16 (absolute error below 2^-22, under 1.3e-6 of the radius there and
+    less beyond) and a five-term series below it: r within 2e-6 of itself.
+    The angle comes from the 1024-entry table with quadratic angle addition
+    (under 1e-7 absolute): x, y within 5e-7 absolute at r ~ 1."""
     n = 1 << 24
     idx = np.arange(n, dtype=np.uint64)
     w = np.stack([(idx << np.uint64(8)).astype(np.uint32), np.zeros(n, np.uint32)], axis=1)
@@ -64,14 +68,14 @@ def test_b1_accurate_every_lattice_radius_and_angle():
     assert np.all(g[:, 0] == 0.0)
     assert g[0, 1] == 0.0                                   # u = 0: r = 0
     rel = np.abs(g[1:, 1] - ref[1:, 1]) / ref[1:, 1]
-    assert rel.max() <= 4e-7, f"radius: max relative error {rel.max():.3e} at k = {int(np.argmax(rel)) + 1}"
+    assert rel.max() <= 2e-6, f"radius: max relative error {rel.max():.3e} at k = {int(np.argmax(rel)) + 1}"
     k0 = int(LP.M24 * (1.0 - np.exp(-0.5)))
     w = np.stack([np.full(n, k0 << 8, np.uint32), (idx << np.uint64(8)).astype(np.uint32)], axis=1)
     got, _ = nr.nrng_eval_points(nr.B1, torch.from_numpy(w.view(np.int32)).cuda(), 0.0, 1.0, "accurate")
     g = got.cpu().numpy().astype(np.float64)
     ref = oracle.b1_points(np.full(n, k0 * 2.0 ** -24), u, 0.0, 1.0)
     err = np.abs(g - ref).max()
-    assert err <= 3e-7, f"angle: max absolute error {err:.3e}"
+    assert err <= 5e-7, f"angle: max absolute error {err:.3e}"
 
 
 def polar_points():

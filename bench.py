@@ -517,6 +517,39 @@ def write_ceiling(buf, K, W):
     return res
 
 
+def philox_ceiling(step, K, W):
+    """The rate this GPU draws Philox4x32-10 blocks with no output traffic
+    (nrng_philox_ceiling over the 2^26 blocks of a 2^28-normal B1 stream):
+    the instruction ceiling every generator here shares."""
+    import torch
+    nr = step.nr
+    acc = torch.zeros(1, dtype=torch.int32, device=step.out_b1.device)
+    nblocks = N_FULL // 4
+
+    def run():
+        nr.nrng_philox_ceiling(acc, nblocks, KEY, step.base)
+    for _ in range(W):
+        run()
+    ms, stats = timed_launches(run, K)
+    return {"nblocks": nblocks, "ms": round(ms, 4), "blocks_per_s": nblocks / (ms * 1e-3), **stats,
+            "b1_normals_per_s": 4.0 * nblocks / (ms * 1e-3),
+            "polar_normals_per_s": math.pi * nblocks / (ms * 1e-3),
+            "source": "measured: nrng_philox_ceiling, CUDA events"}
+
+
+def tighter_bound(normals_per_s, bytes_per_normal, normals_per_block, ceiling, ph):
+    """normals/s against the tighter of the measured write ceiling and the
+    measured Philox ceiling (normals_per_block normals per Philox block)."""
+    if not ceiling or not ph:
+        return None
+    wc = max(v for v in (ceiling.get("fill_GB_per_s"), ceiling.get("memset_GB_per_s")) if v)
+    b_write = wc * 1e9 / bytes_per_normal
+    b_philox = ph["blocks_per_s"] * normals_per_block
+    bound, which = (b_write, "hbm write ceiling") if b_write <= b_philox else (b_philox, "philox ceiling")
+    return {"bound": which, "normals_per_s": bound, "frac": round(normals_per_s / bound, 4),
+            "write_ceiling_normals_per_s": b_write, "philox_ceiling_normals_per_s": b_philox}
+
+
 def _oracle_work(task):
     """One worker's share of the oracle sample (module level, so that a spawn
     pool can run it): B1 and Polar of n normals each at this worker's own
@@ -815,27 +848,62 @@ def bench_ours(args):
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
                 "traffic": recorded_traffic(kernel_names[dom]),
                 "algorithmic_bytes_per_launch": alg_bytes[dom]}
-    # The same kernel against the Philox multiply floor: 20 32x32->64 products
-    # a block at 64 products a clock per SM (two per wide product) is 1.6
-    # blocks a clock per SM.  Algorithmic blocks: n/4 per B1 stream, n/pi per
-    # Polar stream (n/2 pairs at acceptance pi/4, two candidates a block).
-    sm_mhz = clocks.summary().get("sm_mhz") or 2070.0
-    floor = sm_count_of(torch.cuda.current_device()) * sm_mhz * 1e6 * 1.6
-    alg_blocks = {"b1": N_FULL / 4, "polar": N_FULL / math.pi, "batch": step.batch_philox_blocks}
-    roofline_philox = {"kernel": kernel_names[dom], "bound": "alu", "unit": "Philox blocks/s",
-                       "achieved": alg_blocks[dom] / t_dom, "peak": floor,
-                       "frac": round(alg_blocks[dom] / t_dom / floor, 4),
-                       "peak_source": f"derived: SMs x {sm_mhz:.0f} MHz x 1.6 blocks/clock/SM"}
-
     # ---- precision sweep at N = 2^28 (mu 1.5, sigma 0.25): each variant timed
     # alone with CUDA events (mean of K launches after W warm-ups), not part of
     # the step
     sweep = {}
     ceiling = None
+    ph = None
     if not args.no_sweep:
         sweep = precision_sweep(step, K, args.warmup, peak)
         sweep.update(configs_sweep(step, K, args.warmup, peak))
         ceiling = write_ceiling(step.out_b1, K, args.warmup)
+        ph = philox_ceiling(step, K, args.warmup)
+        # every sweep row against the tighter of the two measured ceilings
+        per_block = {"b1": 4.0, "b2": 4.0, "b3": 8.0 / 3.0, "polar": math.pi, "p2": math.pi,
+                     "ratio": 2.0 * (math.pi * math.e) ** 0.5 / 4.0}
+        for name, row in sweep.items():
+            if "normals_per_s" not in row or name.startswith("batched") or name.startswith("c1_"):
+                continue
+            head = name.split("_")[0] if not name.startswith("c2_") else name.split("_")[1]
+            nb = 2 if ("bf16" in name or "f16" in name) else 4
+            tb = tighter_bound(row["normals_per_s"], nb, per_block.get(head, 4.0), ceiling, ph)
+            if tb:
+                row["frac_of_tighter"] = tb["frac"]
+                row["tighter_bound"] = tb["bound"]
+
+    def kernel_roofline(part, kernel, per_block):
+        t = part_ms[part] * 1e-3
+        achieved = alg_bytes[part] / t / 1e9
+        d = {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+             "frac": round(achieved / peak, 4), "peak_source": peak_src, "traffic": recorded_traffic(kernel),
+             "algorithmic_bytes_per_launch": alg_bytes[part]}
+        if ceiling:
+            wc = max(v for v in (ceiling.get("fill_GB_per_s"), ceiling.get("memset_GB_per_s")) if v)
+            d["write_ceiling_GB_per_s"] = wc
+            d["frac_of_write_ceiling"] = round(achieved / wc, 4)
+        tb = tighter_bound(N_FULL / t, 4, per_block, ceiling, ph)
+        if tb:
+            d["tighter"] = tb
+        return d
+    roofline_b1 = kernel_roofline("b1", "k_b1", 4.0)
+    roofline_polar = kernel_roofline("polar", "k_polar", math.pi)
+
+    # The same kernel against the Philox ceiling: the measured rate of
+    # nrng_philox_ceiling when the sweep ran, else derived (20 32x32->64
+    # products a block at 64 products a clock per SM, two per wide product:
+    # 1.6 blocks a clock per SM).  Algorithmic blocks: n/4 per B1 stream, n/pi
+    # per Polar stream (n/2 pairs at acceptance pi/4, two candidates a block).
+    sm_mhz = clocks.summary().get("sm_mhz") or 2070.0
+    alg_blocks = {"b1": N_FULL / 4, "polar": N_FULL / math.pi, "batch": step.batch_philox_blocks}
+    if ph:
+        floor, floor_src = ph["blocks_per_s"], "measured: nrng_philox_ceiling over 2^26 blocks, CUDA events"
+    else:
+        floor = sm_count_of(torch.cuda.current_device()) * sm_mhz * 1e6 * 1.6
+        floor_src = f"derived: SMs x {sm_mhz:.0f} MHz x 1.6 blocks/clock/SM"
+    roofline_philox = {"kernel": kernel_names[dom], "bound": "alu", "unit": "Philox blocks/s",
+                       "achieved": alg_blocks[dom] / t_dom, "peak": floor,
+                       "frac": round(alg_blocks[dom] / t_dom / floor, 4), "peak_source": floor_src}
 
     cpu = None
     os.sched_setaffinity(0, cpus_all)   # the CPU baseline uses every core
@@ -848,8 +916,8 @@ def bench_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (Philox4x32-10 streams; seeded PCG64 inputs)",
             "config": workload_config(world, step.batch_total, step.rep_shape),
-            "parts": parts, "sweep": sweep, "write_ceiling": ceiling, "roofline": roofline,
-            "roofline_philox": roofline_philox,
+            "parts": parts, "sweep": sweep, "write_ceiling": ceiling, "philox_ceiling": ph, "roofline": roofline,
+            "roofline_b1": roofline_b1, "roofline_polar": roofline_polar, "roofline_philox": roofline_philox,
             "clocks": clocks.summary(),
             "e2e": e2e, "gpu_launches": K * step.our_launches_per_step, "cpu_baseline": cpu,
         }

@@ -313,6 +313,7 @@ int32_t nrng_batched_workspace_size(const nrng_stream_desc_t *h_desc, int32_t k,
  * overlap in the output.  The per-stream work is scheduled as tiles pulled
  * from one global work counter; Polar tiles look back within their stream.
  * Descriptor errors found on the device (n < 0, sigma < 0, bad method, a
+ * stream of more than 2^31 work items, i.e. above about 3.5e13 normals, a
  * workspace smaller than the descriptors need) set the status word and the
  * launch writes nothing.  Capturable in a CUDA graph. */
 int32_t nrng_batched(void *d_out, const nrng_stream_desc_t *d_desc, int32_t k,

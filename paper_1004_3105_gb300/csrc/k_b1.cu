@@ -42,7 +42,7 @@ k_b1(T *__restrict__ out, int64_t n, int64_t nblocks, float mu, float sigma, uin
 {
     __shared__ float4 s_tab[MODE == kModeAccurate ? 1024 : 1];
     const float4 *tab = b1_table_to_shared<MODE>(s_tab);
-    const B1Coef cf = b1_coef(mu, sigma);
+    const RadiusCoef cf = radius_coef(mu, sigma);
     const int64_t stride = (int64_t)gridDim.x * kB1Threads;
     for (int64_t b = (int64_t)blockIdx.x * kB1Threads + threadIdx.x; b < nblocks; b += stride) {
         const float4 o = b1_block<MODE>(philox_block(counter + (uint64_t)b, rk), cf, tab);
@@ -71,7 +71,7 @@ k_b1_whole(T *__restrict__ out, int64_t n, uint32_t nwhole, float mu, float sigm
 {
     __shared__ float4 s_tab[MODE == kModeAccurate ? 1024 : 1];
     const float4 *tab = b1_table_to_shared<MODE>(s_tab);
-    const B1Coef cf = b1_coef(mu, sigma);
+    const RadiusCoef cf = radius_coef(mu, sigma);
     const uint32_t stride = gridDim.x * kB1Threads;
     // Two blocks per iteration (b and b + stride): their Philox chains are
     // independent, so one fills the other's dependency stalls.

@@ -11,8 +11,9 @@
 //     overflow item, placed after every stream's primary items, that runs
 //     whatever tiles the stream still needs, one after another;
 //   k_batched (persistent, one global work counter) pulls items in order,
-//     finds the stream by a galloping search over the item prefix and runs a
-//     B1 tile or Polar tiles (look-back within the stream's own status words).
+//     finds the stream in the item table the prep kernel wrote (one load) and
+//     runs a B1 tile or Polar tiles (look-back within the stream's own status
+//     words).
 // Items are handed out in increasing order, a CTA starts an item as soon as
 // it has claimed it, and a stream's tiles are claimed in increasing tile
 // order, so a Polar tile only waits on tiles already owned by running CTAs.
@@ -99,34 +100,49 @@ __host__ __device__ inline void stream_items(const nrng_stream_desc_t &d, int th
         const uint64_t blocks = (uint64_t)(slots * tile_blocks);
         if (d.counter > ULLONG_MAX - (blocks - 1)) items = -2;
     }
+    // the item table keeps a stream's item index in 32 bits
+    if (items > INT_MAX) {
+        items = -1;
+        slots = 0;
+    }
 }
 
 size_t batched_workspace_bytes(const nrng_stream_desc_t *h_desc, int32_t k)
 {
     // Sized for the configuration with the most status slots, so that any
     // configuration (autotuned or pinned) fits the same workspace.
+    // Each configuration needs its tile status words and its item table
+    // (one 8-byte entry per primary item).
     size_t best = 0;
     for (int c = 0; c < kNumConfigs; ++c) {
-        int64_t slots = 0;
+        int64_t slots = 0, items = 0;
         for (int32_t j = 0; j < k; ++j) {
             int64_t it, sl;
             stream_items(h_desc[j], kConfigs[c].threads, kConfigs[c].blocks_per_thread, it, sl);
-            if (it > 0) slots += sl;
+            if (it > 0) {
+                slots += sl;
+                items += it;
+            }
         }
-        best = std::max(best, (size_t)slots);
+        best = std::max(best, (size_t)(slots + items));
     }
-    return batched_layout(k).tile_status + best * sizeof(unsigned long long);
+    return batched_layout(k).tile_status + best * 8;
 }
 
 // ------------------------------------------------------------ prep --------
 // One CTA: every thread takes a contiguous run of descriptors, sums their
 // items and status slots, and one block-wide exclusive scan places them.
+// Then every thread writes the item table entries of its streams: entry i
+// of the table is (stream, item of the stream) for primary item i, so that a
+// claim finds its stream with one load.  The table follows the tile status
+// words; its byte offset goes to the header (aux[2]).
 constexpr int kPrepThreads = 1024;
 
 __global__ void __launch_bounds__(kPrepThreads)
 k_batched_prep(BatchedParams bp, int threads, int bpt)
 {
     __shared__ long long s_wi[kPrepThreads / 32], s_ws[kPrepThreads / 32];
+    __shared__ long long s_tot_items, s_tot_slots;
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_bad = 0;
@@ -187,8 +203,17 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
         }
         s_wi[lane] = wi - wi0;   // exclusive warp offsets
         s_ws[lane] = ws - ws0;
+        if (lane == 31) {
+            s_tot_items = wi;
+            s_tot_slots = ws;
+        }
     }
     __syncthreads();
+    // the item table after the status words of every Polar stream; written
+    // only when the workspace holds it (else the status word reports it)
+    const size_t table_off = batched_layout(bp.k).tile_status + (size_t)s_tot_slots * 8;
+    const bool table_fits = table_off + (size_t)s_tot_items * 8 <= bp.ws_bytes;
+    int2 *table = reinterpret_cast<int2 *>(reinterpret_cast<char *>(bp.hdr) + table_off);
     long long ci = s_wi[warp] + ii - mi, cs = s_ws[warp] + is - ms;   // exclusive for this thread
 #pragma unroll
     for (int q = 0; q < kKeep; ++q) {
@@ -196,6 +221,8 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
         if (j >= j1) continue;
         bp.item_prefix[j] = ci;
         bp.slot_base[j] = cs;
+        if (table_fits)
+            for (int64_t it = 0; it < keep_items[q]; ++it) table[ci + it] = make_int2(j, (int)it);
         ci += keep_items[q];
         cs += keep_slots[q];
     }
@@ -205,14 +232,15 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
         if (items < 0) { items = 0; slots = 0; }
         bp.item_prefix[j] = ci;
         bp.slot_base[j] = cs;
+        if (table_fits)
+            for (int64_t it = 0; it < items; ++it) table[ci + it] = make_int2(j, (int)it);
         ci += items;
         cs += slots;
     }
     if (tid == kPrepThreads - 1) {
         bp.item_prefix[bp.k] = ci;
-        const size_t need = batched_layout(bp.k).tile_status + (size_t)cs * 8;
         int bad = s_bad;
-        if (!bad && need > bp.ws_bytes) bad = kStatusWorkspace;
+        if (!bad && !table_fits) bad = kStatusWorkspace;
         if (bad) {
             bp.hdr->status = bad;
             bp.hdr->done = 1;
@@ -222,6 +250,7 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
             // primary items, then one overflow item per stream
             bp.hdr->aux[0] = (unsigned long long)ci + (unsigned long long)bp.k;
             bp.hdr->aux[1] = (unsigned long long)ci;
+            bp.hdr->aux[2] = (unsigned long long)table_off;
         }
     }
 }
@@ -234,7 +263,7 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
 // count (128 x 16: six CTAs, up to 80 registers a thread; 128 x 12: eight, 64).
 template <int THREADS, int BPT, int MODE>
 struct BatchedOccupancy {
-    static constexpr int kSmemBlocks = (228 * 1024) / ((int)sizeof(PolarSmem<THREADS, BPT>) + 1024 + 256);
+    static constexpr int kSmemBlocks = (228 * 1024) / ((int)sizeof(RejSmem<THREADS / 32, BPT>) + 1024 + 256);
     static constexpr int kThreadBlocks = 1024 / THREADS;
     static constexpr int kMin = kSmemBlocks < kThreadBlocks ? kSmemBlocks : kThreadBlocks;
     static constexpr int kMinBlocks = kMin > 0 ? kMin : 1;
@@ -250,12 +279,12 @@ struct BatchedWork {
 };
 
 // Claims the next item and resolves it to a stream and tile range (one
-// thread).  Items [0, primary) are the streams' primary tiles in stream
-// order; item primary + j is stream j's overflow item.  `last` is the stream
-// of this CTA's previous primary item: items only increase, so the search
-// gallops up from it.
-__device__ __forceinline__ void batched_claim(const BatchedParams &bp, unsigned long long total_items,
-                                              unsigned long long primary, int cand, int &last, BatchedWork &w)
+// thread).  Items [0, primary) are the streams' primary items in stream
+// order, found in the item table with one load; item primary + j is stream
+// j's overflow item.
+__device__ __forceinline__ void batched_claim(const BatchedParams &bp, const int2 *table,
+                                              unsigned long long total_items, unsigned long long primary, int cand,
+                                              BatchedWork &w)
 {
     // The error flag and the claim are issued together (one round trip, not
     // two); an item claimed after an error is dropped unprocessed.  This flag
@@ -271,23 +300,9 @@ __device__ __forceinline__ void batched_claim(const BatchedParams &bp, unsigned 
     }
     int j;
     if ((unsigned long long)item < primary) {
-        // largest j with item_prefix[j] <= item (empty streams share a prefix
-        // with the next one; the largest j is the non-empty one)
-        int lo = last, step = 1, hi;
-        for (;;) {
-            hi = lo + step;
-            if (hi >= bp.k) { hi = bp.k; break; }
-            if (bp.item_prefix[hi] > item) break;
-            lo = hi;
-            step <<= 1;
-        }
-        while (hi - lo > 1) {   // prefix[lo] <= item < prefix[hi]
-            const int mid = (lo + hi) >> 1;
-            if (bp.item_prefix[mid] <= item) lo = mid; else hi = mid;
-        }
-        j = lo;
-        last = lo;
-        w.t0 = item - bp.item_prefix[j];
+        const int2 e = table[item];
+        j = e.x;
+        w.t0 = e.y;
         w.t1 = w.t0 + 1;
         w.overflow = 0;
     } else {
@@ -310,16 +325,16 @@ __global__ void __launch_bounds__(THREADS, (BatchedOccupancy<THREADS, BPT, MODE>
 k_batched(BatchedParams bp)
 {
     constexpr int kCand = 2 * THREADS * BPT;
-    __shared__ PolarSmem<THREADS, BPT> sm;
+    __shared__ RejSmem<THREADS / 32, BPT> sm;
     __shared__ BatchedWork s_work;
     __shared__ int s_done;
 
     const unsigned long long total_items = bp.hdr->aux[0];
     const unsigned long long primary = bp.hdr->aux[1];
+    const int2 *table = reinterpret_cast<const int2 *>(reinterpret_cast<const char *>(bp.hdr) + bp.hdr->aux[2]);
     char *out_base = static_cast<char *>(bp.out);
-    int last = 0;   // thread 0: stream of the previous primary item
     for (;;) {
-        if (threadIdx.x == 0) batched_claim(bp, total_items, primary, kCand, last, s_work);
+        if (threadIdx.x == 0) batched_claim(bp, table, total_items, primary, kCand, s_work);
         __syncthreads();
         const int j = s_work.stream;
         if (j < 0) break;
@@ -335,22 +350,21 @@ k_batched(BatchedParams bp)
             if (overflow) {
                 // B1 streams have no overflow tiles
             } else if (((uintptr_t)out % (4 * sizeof(T))) == 0) {
-                const B1Coef cf = b1_coef(d.mu, d.sigma);
+                const RadiusCoef cf = radius_coef(d.mu, d.sigma);
                 for (int q = 0; q < kB1TilesPerItem; ++q)
                     b1_tile<THREADS, BPT, MODE, T, true>(out, d.n, cf, kSinCos1024, rk, d.counter,
                                                          t0 * kB1TilesPerItem + q);
             } else {
-                const B1Coef cf = b1_coef(d.mu, d.sigma);
+                const RadiusCoef cf = radius_coef(d.mu, d.sigma);
                 for (int q = 0; q < kB1TilesPerItem; ++q)
                     b1_tile<THREADS, BPT, MODE, T, false>(out, d.n, cf, kSinCos1024, rk, d.counter,
                                                           t0 * kB1TilesPerItem + q);
             }
         } else if (!(overflow && skip)) {
+            const RadiusCoef cf = radius_coef(d.mu, d.sigma);
             PolarStream ps;
             ps.n = d.n;
             ps.nitems = (d.n + 1) / 2;
-            ps.mu = d.mu;
-            ps.sigma = d.sigma;
             ps.counter = d.counter;
             ps.status = bp.tile_status + bp.slot_base[j];
             ps.tiles_max = polar_tiles_for(d.n, kCand);
@@ -372,9 +386,11 @@ k_batched(BatchedParams bp)
                     // Stream complete: every later tile's prefix is >= nitems.
                     if (threadIdx.x == 0) st_relaxed(ps.status + t, kFlagPrefix | (unsigned long long)ps.nitems);
                 } else if (aligned) {
-                    ok = polar_tile<THREADS, BPT, MODE, T, true>(sm, out, ps, rk, t, bp.hdr, bp.spin_limit_ns);
+                    ok = reject_tile<PolarPolicy<MODE>, THREADS / 32, BPT, T, true, true>(sm, out, ps, rk, cf, t, bp.hdr,
+                                                                                         bp.spin_limit_ns);
                 } else {
-                    ok = polar_tile<THREADS, BPT, MODE, T, false>(sm, out, ps, rk, t, bp.hdr, bp.spin_limit_ns);
+                    ok = reject_tile<PolarPolicy<MODE>, THREADS / 32, BPT, T, false, true>(sm, out, ps, rk, cf, t, bp.hdr,
+                                                                                          bp.spin_limit_ns);
                 }
                 __syncthreads();
                 if (!ok) break;

@@ -63,11 +63,13 @@ cudaError_t launch_b3(void *out, int64_t n, float mu, float sigma, uint64_t key,
 }
 
 // --------------------------------------------------------------- P2 and R --
-template <class Policy, int OCC_THREADS, typename T>
+template <class Policy, typename T>
 static cudaError_t reject_launch_t(const PolarParams &p, bool aligned, cudaStream_t s)
 {
     static std::atomic<int> occ_a{0}, occ_p{0};
-    auto kern = aligned ? k_reject<Policy, OCC_THREADS, T, true> : k_reject<Policy, OCC_THREADS, T, false>;
+    const bool cf = reject_carry_free(p.counter, p.tiles_max);
+    auto kern = aligned ? (cf ? k_reject<Policy, T, true, false> : k_reject<Policy, T, true, true>)
+                        : (cf ? k_reject<Policy, T, false, false> : k_reject<Policy, T, false, true>);
     int occ = 0;
     const cudaError_t e = cached_occupancy(aligned ? occ_a : occ_p, kern, kPolarThreads, occ);
     if (e != cudaSuccess) return e;
@@ -76,21 +78,21 @@ static cudaError_t reject_launch_t(const PolarParams &p, bool aligned, cudaStrea
     return cudaGetLastError();
 }
 
-template <class Policy, int OCC_THREADS>
+template <class Policy>
 static cudaError_t reject_launch(const PolarParams &p, int dtype, bool aligned, size_t ws_used, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(p.hdr, 0, ws_used, s);
     if (e != cudaSuccess) return e;
     switch (dtype) {
-    case NRNG_F32: return reject_launch_t<Policy, OCC_THREADS, float>(p, aligned, s);
-    case NRNG_BF16: return reject_launch_t<Policy, OCC_THREADS, __nv_bfloat16>(p, aligned, s);
-    default: return reject_launch_t<Policy, OCC_THREADS, __half>(p, aligned, s);
+    case NRNG_F32: return reject_launch_t<Policy, float>(p, aligned, s);
+    case NRNG_BF16: return reject_launch_t<Policy, __nv_bfloat16>(p, aligned, s);
+    default: return reject_launch_t<Policy, __half>(p, aligned, s);
     }
 }
 
 cudaError_t launch_polar_p2(const PolarParams &p, int dtype, bool aligned, cudaStream_t s)
 {
-    return reject_launch<P2Policy, 1280>(p, dtype, aligned, polar_workspace_bytes(p.n), s);
+    return reject_launch<P2Policy>(p, dtype, aligned, polar_workspace_bytes(p.n), s);
 }
 
 int64_t ratio_tiles_max(int64_t n)
@@ -107,8 +109,8 @@ size_t ratio_workspace_bytes(int64_t n)
 cudaError_t launch_ratio(const PolarParams &p, int dtype, int mode, bool aligned, cudaStream_t s)
 {
     if (mode == kModeFast)
-        return reject_launch<RatioPolicy<kModeFast>, 1280>(p, dtype, aligned, ratio_workspace_bytes(p.n), s);
-    return reject_launch<RatioPolicy<kModeAccurate>, 1280>(p, dtype, aligned, ratio_workspace_bytes(p.n), s);
+        return reject_launch<RatioPolicy<kModeFast>>(p, dtype, aligned, ratio_workspace_bytes(p.n), s);
+    return reject_launch<RatioPolicy<kModeAccurate>>(p, dtype, aligned, ratio_workspace_bytes(p.n), s);
 }
 
 }  // namespace nrng

@@ -41,7 +41,7 @@ k_eval_points(int kind, const uint32_t *__restrict__ in, int64_t n, float mu, fl
         } else {
             const uint32_t a = in[2 * i], b = in[2 * i + 1];
             if (kind == kPointsB1) {
-                b1_pair<MODE>(a, b, b1_coef(mu, sigma), kSinCos1024, x, y);
+                b1_pair<MODE>(a, b, radius_coef(mu, sigma), kSinCos1024, x, y);
             } else if (kind == kPointsRatio) {
                 int2 ab;
                 ok = ratio_accept(a, b, ab) ? 1 : 0;
@@ -53,7 +53,7 @@ k_eval_points(int kind, const uint32_t *__restrict__ in, int64_t n, float mu, fl
                 if (kind == kPointsP2)
                     p2_pair(kx, ky, mu, sigma, x, y);
                 else if (MODE != kModeB2)   // B2 is a B1 mode only
-                    polar_pair<MODE == kModeFast ? kModeFast : kModeAccurate>(kx, ky, mu, sigma, x, y);
+                    polar_pair<MODE == kModeFast ? kModeFast : kModeAccurate>(kx * 256, ky * 256, radius_coef(mu, sigma), x, y);
             }
         }
         if (accept) accept[i] = ok;

@@ -7,11 +7,11 @@
 // look-back scan over tiles of kPolarCandPerTile candidates (k_reject and
 // reject_tile in tiles.cuh, with Algorithm P's policy): a persistent CTA takes the next tile id from a global counter
 // (dynamic ids, so a tile only ever waits on tiles already owned by running
-// CTAs); each warp draws its candidates, tests 0 < kx'^2 + ky'^2 < 2^46
-// exactly in 64-bit integers, compacts the accepted ones into its own
-// shared-memory segment by ballot/popc rank, runs step 4 densely over it and,
-// once warp 0 has looked back for the tile's prefix, copies its runs to their
-// global positions.  The tile holding the ceil(n/2)-th accepted pair writes
+// CTAs); each warp draws its contiguous run of candidates, tests
+// 0 < kx'^2 + ky'^2 < 2^46 exactly in 64-bit integers, compacts the accepted
+// ones into its own shared-memory segment by ballot/popc rank, runs step 4
+// densely over it and, once warp 0 has looked back for the tile's prefix,
+// copies the segment to its place in the output as one dense run.  The tile holding the ceil(n/2)-th accepted pair writes
 // next_counter and raises `done`, after which CTAs stop taking tiles.
 #include <algorithm>
 
@@ -34,7 +34,9 @@ template <int MODE, typename T>
 static cudaError_t polar_launch_t(const PolarParams &p, bool aligned, cudaStream_t s)
 {
     static std::atomic<int> occ_aligned{0}, occ_plain{0};
-    auto kern = aligned ? k_reject<PolarPolicy<MODE>, 1536, T, true> : k_reject<PolarPolicy<MODE>, 1536, T, false>;
+    const bool cf = reject_carry_free(p.counter, p.tiles_max);
+    auto kern = aligned ? (cf ? k_reject<PolarPolicy<MODE>, T, true, false> : k_reject<PolarPolicy<MODE>, T, true, true>)
+                        : (cf ? k_reject<PolarPolicy<MODE>, T, false, false> : k_reject<PolarPolicy<MODE>, T, false, true>);
     int occ = 0;
     const cudaError_t e = cached_occupancy(aligned ? occ_aligned : occ_plain, kern, kPolarThreads, occ);
     if (e != cudaSuccess) return e;
@@ -138,15 +140,14 @@ k_polar_scan(const int *__restrict__ counts, long long *__restrict__ prefix, int
 }
 
 template <int MODE, typename T, bool ALIGNED>
-__global__ void __launch_bounds__(kPolarThreads, (PolarOccupancy<kPolarThreads, MODE>::kMinBlocks))
+__global__ void __launch_bounds__(kPolarThreads, (RejOccupancy<kRejWarps, kRejRows>::kMinBlocks))
 k_polar_write(const PolarParams p, const long long *__restrict__ prefix)
 {
-    __shared__ PolarSmem<kPolarThreads, kPolarRows> sm;
+    __shared__ RejSmem<kRejWarps, kRejRows> sm;
+    const RadiusCoef cf = radius_coef(p.mu, p.sigma);
     PolarStream ps;
     ps.n = p.n;
     ps.nitems = p.nitems;
-    ps.mu = p.mu;
-    ps.sigma = p.sigma;
     ps.counter = p.counter;
     ps.status = nullptr;
     ps.tiles_max = p.tiles_max;
@@ -159,8 +160,8 @@ k_polar_write(const PolarParams p, const long long *__restrict__ prefix)
     for (int64_t t = blockIdx.x; t < p.tiles_max; t += gridDim.x) {
         const long long P = prefix[t];   // same value for every thread of the CTA
         if (P >= p.nitems) break;        // prefixes only grow with t
-        polar_tile<kPolarThreads, kPolarRows, MODE, T, ALIGNED, RoundKeys, true>(sm, out, ps, p.rk, t, p.hdr,
-                                                                                p.spin_limit_ns, P);
+        reject_tile<PolarPolicy<MODE>, kRejWarps, kRejRows, T, ALIGNED, true, RoundKeys, true>(sm, out, ps, p.rk, cf, t,
+                                                                                            p.hdr, p.spin_limit_ns, P);
         __syncthreads();
     }
 }

@@ -28,7 +28,7 @@ static int rep_grid(int64_t nblocks)
 template <int MODE>
 __device__ __forceinline__ float4 b1_block_z(uint64_t counter_plus_b, const RoundKeys &rk)
 {
-    return b1_block<MODE>(philox_block(counter_plus_b, rk), b1_coef(0.0f, 1.0f), kSinCos1024);
+    return b1_block<MODE>(philox_block(counter_plus_b, rk), radius_coef(0.0f, 1.0f), kSinCos1024);
 }
 
 __device__ __forceinline__ float comp(const float4 &v, int j)

@@ -41,8 +41,12 @@ struct WsHeader {
 static_assert(sizeof(WsHeader) == 64, "workspace header is 64 bytes");
 
 // ---------------------------------------------------------------- Polar --
-constexpr int kPolarThreads = 256;
-constexpr int kPolarRows = 8;                                  // Philox blocks per thread per tile
+// Tile of the single-stream rejection kernels (Algorithm P, Method P2,
+// Algorithm R): kRejWarps warps x kRejRows rows x 32 lanes x 2 candidates.
+constexpr int kRejWarps = 4;
+constexpr int kRejRows = 16;
+constexpr int kPolarThreads = kRejWarps * 32;                   // 128
+constexpr int kPolarRows = kRejRows;                            // Philox blocks per thread per tile
 constexpr int kPolarBlocksPerTile = kPolarThreads * kPolarRows; // 2048
 constexpr int kPolarCandPerTile = 2 * kPolarBlocksPerTile;      // 4096
 

@@ -10,7 +10,7 @@ namespace nrng {
 // Blocks [t*TB, (t+1)*TB) of a stream, TB = THREADS * BPT; block b writes
 // out[4b .. 4b+3] (Algorithm B1, two pairs per block).
 template <int THREADS, int BPT, int MODE, typename T, bool ALIGNED, typename Key>
-__device__ __forceinline__ void b1_tile(T *__restrict__ out, int64_t n, const B1Coef &cf, const float4 *tab,
+__device__ __forceinline__ void b1_tile(T *__restrict__ out, int64_t n, const RadiusCoef &cf, const float4 *tab,
                                         const Key &rk, uint64_t counter, int64_t t)
 {
     const int64_t nblocks = (n + 3) / 4;
@@ -43,44 +43,36 @@ __device__ __forceinline__ void b1_tile(T *__restrict__ out, int64_t n, const B1
     }
 }
 
-// Resident threads per SM the Polar tile kernels are compiled for (sets the
-// register budget through __launch_bounds__: 40 registers a thread, without
-// spills).  With the 33.6 KB tile, six 256-thread CTAs fit per SM.
-template <int THREADS, int MODE>
-struct PolarOccupancy {
-    static constexpr int kThreads = 1536;
-    static constexpr int kMinBlocks = (kThreads / THREADS) > 0 ? (kThreads / THREADS) : 1;
+// --------------------------------------------------------- rejection tile --
+// A tile of a rejection stream (Algorithm P, Method P2, Algorithm R) is NW
+// warps x R rows x 32 lanes x 2 candidates.  Candidates are warp-major: warp
+// w of tile t draws the Philox blocks t NW R 32 + w R 32 + r 32 + lane (row r,
+// r = 0 .. R-1), and block b holds the candidates 2b (words 0, 1) and 2b + 1
+// (words 2, 3).  A warp's accepted candidates are then one contiguous run of
+// the stream's accepted candidates, in candidate order: the warp compacts them
+// into its own shared-memory segment, transforms the segment densely, and once
+// the tile's place in the output is known copies it out as one dense run.
+template <int NW, int R>
+struct RejSmem {
+    static constexpr int kSeg = 64 * R;   // most accepted candidates a warp holds
+    int2 seg[NW][kSeg];     // payloads after phase A, output bits after phase C
+    uint2 mask[NW][R];      // accept ballots of (warp, row): half 0, half 1
+    int cnt[NW];            // accepted candidates of each warp
+    int off[NW];            // exclusive offsets of the warps within the tile
+    int total;              // accepted candidates of the tile
+    long long prefix;       // the tile's exclusive prefix (-1 after an error)
+    long long tile;         // the claimed tile id (single-stream kernels)
 };
-
-// --------------------------------------------------------- Polar tile -----
-template <int THREADS, int ROWS>
-struct PolarSmem {
-    static constexpr int kWarps = THREADS / 32;
-    static constexpr int kEntries = ROWS * kWarps;   // (row, warp) segments
-    static constexpr int kSeg = 64 * ROWS;           // most accepted points a warp holds
-    int2 seg[kWarps][kSeg];      // each warp's accepted points in candidate order; step-4 results in place
-    uint2 mask[kEntries];        // (row, warp) accept ballots of the two candidate halves
-    int off[kEntries];           // (row, warp) counts, then exclusive offsets
-    int total;                   // accepted points of the tile
-    long long prefix;
-};
-
-template <int THREADS, int ROWS>
-__device__ __forceinline__ int total_of(const PolarSmem<THREADS, ROWS> &sm, int)
-{
-    return sm.total;
-}
 
 // Where a rejection stream's tile publishes and what it reports.  nitems is
 // the number of accepted candidates the stream needs: ceil(n/2) pairs for
 // P and P2, n values for R.
 struct PolarStream {
     int64_t n, nitems;
-    float mu, sigma;
     uint64_t counter;
     unsigned long long *status;   // this stream's tile status words
     int64_t tiles_max;
-    int *done;                    // set when the last pair is placed
+    int *done;                    // set once the tile holding the last item is known
     uint64_t *next_counter;       // nullable
     int64_t *pair_cand;           // nullable
     long long silent_tile;        // test hook: never publishes (-1: none)
@@ -132,15 +124,61 @@ __device__ __forceinline__ void store_item_bits(T *p, int2 v)
 }
 
 // ------------------------------------------------------------ policies ----
-// Local candidate index (within the tile) of the j-th accepted candidate of
-// row r, warp w, from the row's accept ballots m = (half 0, half 1): the
-// candidates of a row run lane by lane, half 0 before half 1.  Only the
-// careful copy-out (candidate indices requested, or the stream's last tile)
-// needs it, so a binary search over the lanes replaces a stored index per
-// accepted point.
-template <int THREADS>
-__device__ __forceinline__ int accepted_candidate(uint2 m, int j, int r, int w)
+// A rejection method on the candidate stream: each candidate is the two words
+// 2h, 2h+1 of a Philox block (h = 0, 1); accept() decides it exactly and keeps
+// a payload, transform() turns an accepted payload into kOut output values.
+
+// Algorithm P (Sec. 2): steps 2-3 exact on the lattice scaled by 2^8, payload
+// (kx' 2^8, ky' 2^8); step 4 (polar_pair).
+template <int MODE>
+struct PolarPolicy {
+    static constexpr int kOut = 2;
+    __device__ static bool accept(uint32_t wa, uint32_t wb, int2 &pay) { return polar_accept_scaled(wa, wb, pay); }
+    __device__ static void transform(int2 p, const RadiusCoef &c, float &a, float &b)
+    {
+        polar_pair<MODE>(p.x, p.y, c, a, b);
+    }
+};
+
+// Method P2 (Sec. 4): Algorithm P's steps 1-3, step 4a.
+struct P2Policy {
+    static constexpr int kOut = 2;
+    __device__ static bool accept(uint32_t wa, uint32_t wb, int2 &pay) { return polar_accept_scaled(wa, wb, pay); }
+    __device__ static void transform(int2 p, const RadiusCoef &c, float &a, float &b)
+    {
+        p2_pair(p.x >> 8, p.y >> 8, c.mu, c.sigma, a, b);   // exact: multiples of 2^8
+    }
+};
+
+// Algorithm R (Sec. 5): payload (a, b) of the lattice, one value per accept.
+template <int MODE>
+struct RatioPolicy {
+    static constexpr int kOut = 1;
+    __device__ static bool accept(uint32_t wu, uint32_t wv, int2 &pay) { return ratio_accept(wu, wv, pay); }
+    __device__ static void transform(int2 p, const RadiusCoef &c, float &a, float &b)
+    {
+        a = ratio_value<MODE>(p, c.mu, c.sigma);
+        b = 0.0f;
+    }
+};
+
+// Candidate index within the tile of entry e of warp `warp`'s segment, from
+// the (warp, row) accept ballots: the row whose run holds e, then the lane by
+// a binary search over the row's ballots (its candidates run lane by lane,
+// half 0 before half 1).  Only the careful copy-out needs it (candidate
+// indices requested, or the stream's last item).
+template <int NW, int R>
+__device__ __forceinline__ int tile_candidate(const RejSmem<NW, R> &sm, int warp, int e)
 {
+    int rb = 0, r = 0;
+    for (; r < R - 1; ++r) {
+        const uint2 m = sm.mask[warp][r];
+        const int cr = __popc(m.x) + __popc(m.y);
+        if (e < rb + cr) break;
+        rb += cr;
+    }
+    const uint2 m = sm.mask[warp][r];
+    const int j = e - rb;
     int L = 0;   // the lane holding item j: most accepted points below it <= j
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1) {
@@ -150,125 +188,73 @@ __device__ __forceinline__ int accepted_candidate(uint2 m, int j, int r, int w)
     const unsigned lt = (1u << L) - 1u;
     const int before = __popc(m.x & lt) + __popc(m.y & lt);
     const int h = (((m.x >> L) & 1u) && before == j) ? 0 : 1;
-    return 2 * (r * THREADS + w * 32 + L) + h;
+    return 2 * (warp * R * 32 + r * 32 + L) + h;
 }
 
-// A rejection method on the candidate stream: each candidate is the two words
-// 2h, 2h+1 of a Philox block (h = 0, 1); accept() decides it and keeps a
-// payload, transform() turns an accepted payload into kOut output values.
-
-// Algorithm P (Sec. 2): payload (kx', ky'); steps 2-3 exact; step 4.
-template <int MODE>
-struct PolarPolicy {
-    static constexpr int kOut = 2;
-    __device__ static bool accept(uint32_t wa, uint32_t wb, int2 &pay)
-    {
-        const int32_t x = k24(wa), y = k24(wb);
-        pay = make_int2(x, y);
-        int64_t S;
-        return polar_accept(x, y, S);
-    }
-    __device__ static void transform(int2 p, float mu, float sigma, float &a, float &b)
-    {
-        polar_pair<MODE>(p.x, p.y, mu, sigma, a, b);
-    }
-};
-
-// Method P2 (Sec. 4): Algorithm P's steps 1-3, step 4a.
-struct P2Policy {
-    static constexpr int kOut = 2;
-    __device__ static bool accept(uint32_t wa, uint32_t wb, int2 &pay)
-    {
-        return PolarPolicy<kModeAccurate>::accept(wa, wb, pay);
-    }
-    __device__ static void transform(int2 p, float mu, float sigma, float &a, float &b)
-    {
-        p2_pair(p.x, p.y, mu, sigma, a, b);
-    }
-};
-
-// Algorithm R (Sec. 5): payload (a, b) of the lattice, one value per accept.
-template <int MODE>
-struct RatioPolicy {
-    static constexpr int kOut = 1;
-    __device__ static bool accept(uint32_t wu, uint32_t wv, int2 &pay) { return ratio_accept(wu, wv, pay); }
-    __device__ static void transform(int2 p, float mu, float sigma, float &a, float &b)
-    {
-        a = ratio_value<MODE>(p, mu, sigma);
-        b = 0.0f;
-    }
-};
-
 // Tile t of a rejection stream: the method's steps on candidates
-// [t*kCand, (t+1)*kCand) (Algorithm P, P2 or R by Policy), in candidate order
-// (row, warp, lane, half), with the compress done per warp and a decoupled
-// look-back across tiles.
-//   A  each warp draws its rows, runs the accept test, and appends the
-//      accepted payloads to its own shared-memory segment in candidate order
-//      (rank by ballot/popc); lane 0 records each (row, warp) count;
-//   B  warp 0 scans the counts and publishes the tile aggregate at once;
-//   C  each warp runs the transform densely over its own segment, in place;
+// [t kCand, (t+1) kCand) in candidate order, the compress done per warp and a
+// decoupled look-back across tiles.
+//   A  each warp draws its R rows, decides each candidate, and appends the
+//      accepted payloads to its segment in candidate order (rank by
+//      ballot/popc); lane 0 keeps each row's ballots and the warp's count;
+//   B  warp 0 scans the warp counts and publishes the tile aggregate at once;
+//   C  each warp transforms its segment densely, in place;
 //   D  warp 0 looks back for the tile's exclusive prefix P;
-//   E  each warp copies its (row) runs to items P + offset(row, warp) + j
-//      (elements kOut (P + ...)), coalesced.
-// Only A->B and D->E need the whole CTA; the rest is warp-synchronous.
-// Returns false when the look-back gave up (error recorded in hdr).
-// With KNOWN_PREFIX the tile's exclusive prefix is given (known_prefix, from
-// a count pass and a scan): nothing is published and nothing is awaited.
-template <class Policy, int THREADS, int ROWS, typename T, bool ALIGNED, typename Key, bool KNOWN_PREFIX = false>
-__device__ __forceinline__ bool reject_tile(PolarSmem<THREADS, ROWS> &sm, T *__restrict__ out,
-                                            const PolarStream &ps, const Key &rk, int64_t t, WsHeader *hdr,
+//   E  each warp copies its segment to items P + off(warp) + j, coalesced.
+// Returns false when the look-back gave up (error recorded in hdr).  With
+// KNOWN_PREFIX the tile's exclusive prefix is given (from a count pass and a
+// scan): nothing is published and nothing is awaited.  With CARRY false the
+// low counter word of the tile's blocks does not wrap (the caller checks).
+template <class Policy, int NW, int R, typename T, bool ALIGNED, bool CARRY, typename Key, bool KNOWN_PREFIX = false>
+__device__ __forceinline__ bool reject_tile(RejSmem<NW, R> &sm, T *__restrict__ out, const PolarStream &ps,
+                                            const Key &rk, const RadiusCoef &cf, int64_t t, WsHeader *hdr,
                                             unsigned long long limit_ns, long long known_prefix = 0)
 {
-    constexpr int kWarps = THREADS / 32;
-    constexpr int kEntries = ROWS * kWarps;
-    constexpr int kCand = 2 * THREADS * ROWS;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kBPT = NW * R * 32;   // Philox blocks of a tile
+    constexpr int kCand = 2 * kBPT;
+    constexpr int K = Policy::kOut;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool silent = (t == ps.silent_tile);
     const unsigned lt = (1u << lane) - 1u;
-    int2 *seg = sm.seg[warp];
 
     // A: steps 1-3, compacted per warp.
-    int rowbase[ROWS + 1];   // warp-uniform: start of each row's run in the segment
-    int base = 0;
-    const uint64_t b0 = ps.counter + (uint64_t)t * (THREADS * ROWS) + (uint64_t)tid;
+    {
+        const uint64_t c0 = ps.counter + (uint64_t)t * kBPT + (uint64_t)(warp * R * 32 + lane);
+        const uint32_t lo0 = (uint32_t)c0, hi0 = (uint32_t)(c0 >> 32);
+        int2 *seg = sm.seg[warp];
+        int base = 0;
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
-        const uint4 w = philox_block(b0 + (uint64_t)(r * THREADS), rk);
-        int2 p0, p1;
-        const bool a0 = Policy::accept(w.x, w.y, p0);
-        const bool a1 = Policy::accept(w.z, w.w, p1);
-        const unsigned m0 = __ballot_sync(0xFFFFFFFFu, a0);
-        const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1);
-        const int pos = base + __popc(m0 & lt) + __popc(m1 & lt);
-        if (a0) seg[pos] = p0;
-        if (a1) seg[pos + (a0 ? 1 : 0)] = p1;
-        const int cnt = __popc(m0) + __popc(m1);
-        if (lane == 0) {
-            sm.off[r * kWarps + warp] = cnt;
-            sm.mask[r * kWarps + warp] = make_uint2(m0, m1);
+        for (int r = 0; r < R; ++r) {
+            const uint32_t lo = lo0 + (uint32_t)(r * 32);
+            const uint32_t hi = CARRY ? hi0 + (lo < lo0 ? 1u : 0u) : hi0;
+            const uint4 w = philox4x32_10(lo, hi, rk);
+            int2 p0, p1;
+            const bool a0 = Policy::accept(w.x, w.y, p0);
+            const bool a1 = Policy::accept(w.z, w.w, p1);
+            const unsigned m0 = __ballot_sync(0xFFFFFFFFu, a0);
+            const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1);
+            const int pos = base + __popc(m0 & lt) + __popc(m1 & lt);
+            if (a0) seg[pos] = p0;
+            if (a1) seg[pos + (a0 ? 1 : 0)] = p1;
+            if (lane == 0) sm.mask[warp][r] = make_uint2(m0, m1);
+            base += __popc(m0) + __popc(m1);
         }
-        rowbase[r] = base;
-        base += cnt;
+        if (lane == 0) sm.cnt[warp] = base;
     }
-    rowbase[ROWS] = base;
     __syncthreads();
 
-    // B: warp 0 scans the counts (row-major over warps) and publishes.
+    // B: warp 0 scans the warp counts and publishes the aggregate.
     int total = 0;
     if (warp == 0) {
+        const int v = lane < NW ? sm.cnt[lane] : 0;
+        int incl = v;
 #pragma unroll
-        for (int c0 = 0; c0 < kEntries; c0 += 32) {
-            const int v = (c0 + lane < kEntries) ? sm.off[c0 + lane] : 0;
-            int incl = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            if (c0 + lane < kEntries) sm.off[c0 + lane] = total + incl - v;
-            total += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        for (int o = 1; o < NW; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
         }
+        if (lane < NW) sm.off[lane] = incl - v;
+        total = __shfl_sync(0xFFFFFFFFu, incl, NW - 1);
         if (lane == 0) {
             sm.total = total;
             if (!KNOWN_PREFIX && !silent)
@@ -276,106 +262,99 @@ __device__ __forceinline__ bool reject_tile(PolarSmem<THREADS, ROWS> &sm, T *__r
         }
     }
 
-    // C: the transform over this warp's segment, dense, results in place.
-#pragma unroll 2
-    for (int j = lane; j < base; j += 32) {
-        float za, zb;
-        Policy::transform(seg[j], ps.mu, ps.sigma, za, zb);
-        seg[j] = (Policy::kOut == 2) ? pair_bits<T>(za, zb) : item_bits<T>(za);
+    // C: the transform over this warp's segment, dense, results in place
+    // (two entries a lane per step while both are in range).
+    {
+        int2 *q = sm.seg[warp] + lane;
+        int2 *const end = sm.seg[warp] + sm.cnt[warp];
+        for (; q + 32 < end; q += 64) {
+            float za, zb, zc, zd;
+            Policy::transform(q[0], cf, za, zb);
+            Policy::transform(q[32], cf, zc, zd);
+            q[0] = (K == 2) ? pair_bits<T>(za, zb) : item_bits<T>(za);
+            q[32] = (K == 2) ? pair_bits<T>(zc, zd) : item_bits<T>(zc);
+        }
+        if (q < end) {
+            float za, zb;
+            Policy::transform(q[0], cf, za, zb);
+            q[0] = (K == 2) ? pair_bits<T>(za, zb) : item_bits<T>(za);
+        }
     }
 
     // D: warp 0 looks back for the exclusive prefix.
-    if (KNOWN_PREFIX) {
-        if (tid == 0) sm.prefix = known_prefix;
-    } else if (warp == 0) {
-        const long long P = silent ? lookback_warp(ps.status, t, total, hdr, limit_ns, false, false)
-                                   : lookback_warp(ps.status, t, total, hdr, limit_ns, false, true);
+    if (warp == 0) {
+        long long P = known_prefix;
+        if (!KNOWN_PREFIX)
+            P = lookback_warp(ps.status, t, total, hdr, limit_ns, false, !silent);
         if (lane == 0) {
             sm.prefix = P;
-            if (P >= 0 && t == ps.tiles_max - 1 && P + total < ps.nitems) raise_error(hdr, kStatusExhausted);
+            if (P >= 0 && !KNOWN_PREFIX) {
+                if (P < ps.nitems && P + total >= ps.nitems) st_relaxed_s32(ps.done, 1);
+                if (t == ps.tiles_max - 1 && P + total < ps.nitems) raise_error(hdr, kStatusExhausted);
+            }
         }
     }
     __syncthreads();
 
-    // E: run r of this warp -> items P + off(r, warp) + j.
-    constexpr int K = Policy::kOut;
+    // E: this warp's segment -> items P + off(warp) + j.
     const long long P = sm.prefix;
     if (P < 0) return false;
     if (P >= ps.nitems) return true;
-    const int total_t = sm.total;
-    if (ALIGNED && P + total_t < ps.nitems && (K == 1 || P + total_t <= ps.n / 2) && ps.pair_cand == nullptr) {
-        // Every item of the tile is placed whole and nothing else is recorded.
-        T *tile_out = out + K * P;
-#pragma unroll
-        for (int r = 0; r < ROWS; ++r) {
-            const int o = sm.off[r * kWarps + warp];
-            const int rb = rowbase[r];
-            const int cnt = rowbase[r + 1] - rb;   // at most 64: two steps of 32 lanes
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = lane + 32 * h;
-                if (j < cnt) {
-                    if (K == 2) store_pair_bits<T>(tile_out + 2 * (o + j), seg[rb + j], true);
-                    else store_item_bits<T>(tile_out + (o + j), seg[rb + j]);
-                }
+    const long long base = P + sm.off[warp];
+    const int c = sm.cnt[warp];
+    const int2 *seg = sm.seg[warp];
+    if (ALIGNED && base + c <= ps.nitems && (K == 1 || base + c <= ps.n / 2) && ps.pair_cand == nullptr) {
+        // every item of the warp placed whole and nothing else recorded
+        T *o = out + K * (base + lane);
+        const int2 *q = seg + lane;
+        const int2 *const end = seg + c;
+        for (; q + 32 < end; q += 64, o += 64 * K) {
+            const int2 v0 = q[0], v1 = q[32];
+            if (K == 2) {
+                store_pair_bits<T>(o, v0, true);
+                store_pair_bits<T>(o + 64, v1, true);
+            } else {
+                store_item_bits<T>(o, v0);
+                store_item_bits<T>(o + 32, v1);
             }
+        }
+        if (q < end) {
+            if (K == 2) store_pair_bits<T>(o, q[0], true);
+            else store_item_bits<T>(o, q[0]);
         }
         return true;
     }
-    const long long rem = ps.nitems - P;                  // items this tile may still place
-    const long long rem_full = (K == 2) ? ps.n / 2 - P : rem;   // of which with every element
-    const int lim = (int)(rem < kCand ? rem : kCand);
-    const int lim_full = (int)(rem_full < kCand ? (rem_full > 0 ? rem_full : 0) : kCand);
-    T *tile_out = out + K * P;
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
-        const int o = sm.off[r * kWarps + warp];
-        const int cnt = rowbase[r + 1] - rowbase[r];
-        for (int j = lane; j < cnt; j += 32) {
-            const int gl = o + j;   // item index within the tile's output
-            if (gl >= lim) break;
-            const int2 v = seg[rowbase[r] + j];
-            if (K == 1) {
-                store_item_bits<T>(tile_out + gl, v);
-            } else if (ALIGNED) {
-                store_pair_bits<T>(tile_out + 2 * gl, v, gl < lim_full);
-            } else if constexpr (sizeof(T) == 4) {
-                tile_out[2 * gl] = __int_as_float(v.x);
-                if (gl < lim_full) tile_out[2 * gl + 1] = __int_as_float(v.y);
-            } else {
-                const uint16_t lo = (uint16_t)((unsigned)v.x & 0xFFFFu), hi = (uint16_t)((unsigned)v.x >> 16);
-                memcpy(&tile_out[2 * gl], &lo, 2);
-                if (gl < lim_full) memcpy(&tile_out[2 * gl + 1], &hi, 2);
-            }
-            if (ps.pair_cand || gl == lim - 1) {
-                const long long c = t * kCand + accepted_candidate<THREADS>(sm.mask[r * kWarps + warp], j, r, warp);
-                if (ps.pair_cand) ps.pair_cand[P + gl] = c;
-                if (P + gl == ps.nitems - 1) {
-                    if (ps.next_counter) *ps.next_counter = ps.counter + (uint64_t)(c / 2) + 1u;
-                    st_relaxed_s32(ps.done, 1);
-                }
-            }
+    const long long rem_full = (K == 2) ? ps.n / 2 : ps.nitems;   // items with every element
+    for (int e = lane; e < c; e += 32) {
+        const long long g = base + e;
+        if (g >= ps.nitems) break;
+        const int2 v = seg[e];
+        if (K == 1) {
+            store_item_bits<T>(out + g, v);
+        } else if (ALIGNED) {
+            store_pair_bits<T>(out + 2 * g, v, g < rem_full);
+        } else if constexpr (sizeof(T) == 4) {
+            out[2 * g] = __int_as_float(v.x);
+            if (g < rem_full) out[2 * g + 1] = __int_as_float(v.y);
+        } else {
+            const uint16_t lo = (uint16_t)((unsigned)v.x & 0xFFFFu), hi = (uint16_t)((unsigned)v.x >> 16);
+            memcpy(&out[2 * g], &lo, 2);
+            if (g < rem_full) memcpy(&out[2 * g + 1], &hi, 2);
+        }
+        if (ps.pair_cand || g == ps.nitems - 1) {
+            const long long cand = t * kCand + tile_candidate<NW, R>(sm, warp, e);
+            if (ps.pair_cand) ps.pair_cand[g] = cand;
+            if (g == ps.nitems - 1 && ps.next_counter) *ps.next_counter = ps.counter + (uint64_t)(cand / 2) + 1u;
         }
     }
     return true;
-}
-
-// Algorithm P's tile (the common case, for the single-stream and batched kernels).
-template <int THREADS, int ROWS, int MODE, typename T, bool ALIGNED, typename Key, bool KNOWN_PREFIX = false>
-__device__ __forceinline__ bool polar_tile(PolarSmem<THREADS, ROWS> &sm, T *__restrict__ out,
-                                           const PolarStream &ps, const Key &rk, int64_t t, WsHeader *hdr,
-                                           unsigned long long limit_ns, long long known_prefix = 0)
-{
-    return reject_tile<PolarPolicy<MODE>, THREADS, ROWS, T, ALIGNED, Key, KNOWN_PREFIX>(sm, out, ps, rk, t, hdr,
-                                                                                        limit_ns, known_prefix);
 }
 
 // Next tile id of a single rejection stream, or -1 once the stream is
 // complete or the tile budget is spent.
 // The completion flag is read before the claim, never alongside it: a tile
 // claimed and then dropped would never publish, and a later tile's look-back
-// would wait on it until its limit.  (Issuing the two together was measured:
-// an occasional call ran into that wait.)
+// would wait on it until its limit.
 __device__ __forceinline__ long long claim_tile(const PolarParams &p)
 {
     if (ld_relaxed_s32(&p.hdr->done) != 0) return -1;
@@ -383,24 +362,28 @@ __device__ __forceinline__ long long claim_tile(const PolarParams &p)
     return t < p.tiles_max ? t : -1;
 }
 
+// Resident CTAs per SM a rejection kernel is compiled for: as many as the
+// tile's shared memory admits (with the 1 KB the runtime keeps per CTA), so
+// that the register budget follows from that count.
+template <int NW, int R>
+struct RejOccupancy {
+    static constexpr int kSmem = (228 * 1024) / ((int)sizeof(RejSmem<NW, R>) + 1024);
+    static constexpr int kThreads = 2048 / (NW * 32);
+    static constexpr int kMin0 = kSmem < kThreads ? kSmem : kThreads;
+    static constexpr int kMinBlocks = kMin0 > 0 ? kMin0 : 1;
+};
+
 // One rejection stream over the whole grid: persistent CTAs take tile ids
 // from the workspace counter until the stream is complete (done) or the tile
 // budget is spent.
-// OCC_THREADS: resident threads per SM the kernel is compiled for (its
-// register budget): 1536 (40 registers) for Algorithm P, 1280 (48) for the
-// P2 and R transforms, measured faster at those budgets.
-template <class Policy, int OCC_THREADS, typename T, bool ALIGNED>
-__global__ void __launch_bounds__(kPolarThreads, OCC_THREADS / kPolarThreads)
+template <class Policy, typename T, bool ALIGNED, bool CARRY>
+__global__ void __launch_bounds__(kRejWarps * 32, (RejOccupancy<kRejWarps, kRejRows>::kMinBlocks))
 k_reject(const PolarParams p)
 {
-    __shared__ PolarSmem<kPolarThreads, kPolarRows> sm;
-    __shared__ long long s_tile;
-
+    __shared__ RejSmem<kRejWarps, kRejRows> sm;
     PolarStream ps;
     ps.n = p.n;
     ps.nitems = p.nitems;
-    ps.mu = p.mu;
-    ps.sigma = p.sigma;
     ps.counter = p.counter;
     ps.status = p.tile_status;
     ps.tiles_max = p.tiles_max;
@@ -408,18 +391,25 @@ k_reject(const PolarParams p)
     ps.next_counter = p.next_counter;
     ps.pair_cand = p.pair_cand;
     ps.silent_tile = p.debug_silent_tile;
+    const RadiusCoef cf = radius_coef(p.mu, p.sigma);
     T *out = static_cast<T *>(p.out);
-
     for (;;) {
-        if (threadIdx.x == 0) s_tile = claim_tile(p);
+        if (threadIdx.x == 0) sm.tile = claim_tile(p);
         __syncthreads();
-        const long long t = s_tile;
+        const long long t = sm.tile;
         if (t < 0) break;
-        const bool ok = reject_tile<Policy, kPolarThreads, kPolarRows, T, ALIGNED>(sm, out, ps, p.rk, t, p.hdr,
+        const bool ok = reject_tile<Policy, kRejWarps, kRejRows, T, ALIGNED, CARRY>(sm, out, ps, p.rk, cf, t, p.hdr,
                                                                                  p.spin_limit_ns);
         __syncthreads();
         if (!ok) break;
     }
+}
+
+// Whether the low counter word of every Philox block of a rejection stream's
+// tile budget stays below 2^32 (the kernels' carry-free form).
+__host__ __device__ inline bool reject_carry_free(uint64_t counter, int64_t tiles_max)
+{
+    return (uint64_t)(uint32_t)counter + (uint64_t)tiles_max * (uint64_t)kPolarBlocksPerTile <= (uint64_t(1) << 32);
 }
 
 }  // namespace nrng

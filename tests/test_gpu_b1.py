@@ -91,3 +91,14 @@ def test_boxmuller_stream_continuation():
     nr.nrng_boxmuller(c, 0.0, 1.0, 5, 100 + 512)
     sync()
     assert torch.equal(a, torch.cat([b, c]))
+
+
+@pytest.mark.parametrize("nblocks,counter", [(1, 0), (100003, 5), (1 << 20, (7 << 32) + 11)])
+def test_philox_ceiling_draws_every_block(nblocks, counter):
+    # the measurement kernel draws exactly the blocks [counter, counter + nblocks):
+    # the xor of all their words equals the oracle's
+    acc = torch.zeros(1, dtype=torch.int32, device="cuda")
+    nr.nrng_philox_ceiling(acc, nblocks, W.KEY_MAIN, counter)
+    sync()
+    want = int(np.bitwise_xor.reduce(oracle.philox_blocks(nblocks, W.KEY_MAIN, counter).astype(np.uint32).ravel()))
+    assert (int(acc.item()) & 0xFFFFFFFF) == want

@@ -99,7 +99,10 @@ def polar_points():
 def test_polar_accurate_radius():
     """ln s of the accurate Polar path at every S = k^2 (0 < k < 2^23, so s
     runs from 2^-46 to 1 - 2^-22) and at 4 M random lattice points: the
-    radius |(x, y) - mu| within 5e-7 of itself against the oracle."""
+    radius |(x, y) - mu| within 2e-6 of itself against the oracle.  Below
+    1 - s = 1/16 the path takes a series in the exact complement; above it
+    the hardware log2 of s, whose absolute error (under 2^-22) is at most
+    1.3e-6 of the radius at 1 - s = 1/16 and less beyond."""
     k = np.arange(1, 1 << 23, dtype=np.int64)
     rng = np.random.Generator(np.random.PCG64(21))
     rnd = rng.integers(-(1 << 23), 1 << 23, (1 << 22, 2))
@@ -112,7 +115,7 @@ def test_polar_accurate_radius():
     ref = oracle.polar_points(p[:, 0], p[:, 1], 0.0, 1.0)
     r_got, r_ref = np.hypot(g[:, 0], g[:, 1]), np.hypot(ref[:, 0], ref[:, 1])
     rel = np.abs(r_got - r_ref) / r_ref
-    assert rel.max() <= 5e-7, f"max relative radius error {rel.max():.3e} at {p[int(np.argmax(rel))]}"
+    assert rel.max() <= 2e-6, f"max relative radius error {rel.max():.3e} at {p[int(np.argmax(rel))]}"
 
 
 @pytest.mark.parametrize("mode", ["accurate", "fast"])

@@ -347,18 +347,27 @@ k_batched(BatchedParams bp)
         T *out = reinterpret_cast<T *>(out_base) + d.offset;
         bool ok = true;
         if (d.method == NRNG_B1) {
+            const RadiusCoef cf = radius_coef(d.mu, d.sigma);
+            // the item's blocks [first, first + span): carry-free when the low
+            // counter word does not wrap over them
+            constexpr int64_t kSpan = (int64_t)THREADS * BPT * kB1TilesPerItem;
+            const uint64_t first = d.counter + (uint64_t)(t0 * kSpan);
+            const bool carry_free = (uint64_t)(uint32_t)first + (uint64_t)kSpan <= (uint64_t(1) << 32);
             if (overflow) {
                 // B1 streams have no overflow tiles
             } else if (((uintptr_t)out % (4 * sizeof(T))) == 0) {
-                const RadiusCoef cf = radius_coef(d.mu, d.sigma);
-                for (int q = 0; q < kB1TilesPerItem; ++q)
-                    b1_tile<THREADS, BPT, MODE, T, true>(out, d.n, cf, kSinCos1024, rk, d.counter,
-                                                         t0 * kB1TilesPerItem + q);
+                if (carry_free)
+                    for (int q = 0; q < kB1TilesPerItem; ++q)
+                        b1_tile<THREADS, BPT, MODE, T, true, false>(out, d.n, cf, kSinCos1024, rk, d.counter,
+                                                                    t0 * kB1TilesPerItem + q);
+                else
+                    for (int q = 0; q < kB1TilesPerItem; ++q)
+                        b1_tile<THREADS, BPT, MODE, T, true, true>(out, d.n, cf, kSinCos1024, rk, d.counter,
+                                                                   t0 * kB1TilesPerItem + q);
             } else {
-                const RadiusCoef cf = radius_coef(d.mu, d.sigma);
                 for (int q = 0; q < kB1TilesPerItem; ++q)
-                    b1_tile<THREADS, BPT, MODE, T, false>(out, d.n, cf, kSinCos1024, rk, d.counter,
-                                                          t0 * kB1TilesPerItem + q);
+                    b1_tile<THREADS, BPT, MODE, T, false, true>(out, d.n, cf, kSinCos1024, rk, d.counter,
+                                                                t0 * kB1TilesPerItem + q);
             }
         } else if (!(overflow && skip)) {
             const RadiusCoef cf = radius_coef(d.mu, d.sigma);

@@ -8,20 +8,33 @@ namespace nrng {
 
 // ----------------------------------------------------------- B1 tile ------
 // Blocks [t*TB, (t+1)*TB) of a stream, TB = THREADS * BPT; block b writes
-// out[4b .. 4b+3] (Algorithm B1, two pairs per block).
-template <int THREADS, int BPT, int MODE, typename T, bool ALIGNED, typename Key>
+// out[4b .. 4b+3] (Algorithm B1, two pairs per block).  With CARRY false the
+// low counter word of the tile's blocks does not wrap (the caller checks), so
+// the block index and the counter stay 32-bit.
+template <int THREADS, int BPT, int MODE, typename T, bool ALIGNED, bool CARRY, typename Key>
 __device__ __forceinline__ void b1_tile(T *__restrict__ out, int64_t n, const RadiusCoef &cf, const float4 *tab,
                                         const Key &rk, uint64_t counter, int64_t t)
 {
     const int64_t nblocks = (n + 3) / 4;
+    const int64_t b00 = t * (THREADS * BPT) + threadIdx.x;
+    const uint64_t c00 = counter + (uint64_t)b00;
+    const uint32_t lo00 = (uint32_t)c00, hi00 = (uint32_t)(c00 >> 32);
     // Two rows per step when both are in range: the two Philox chains are
     // independent and fill each other's multiply stalls.
     for (int r = 0; r < BPT; r += 2) {
-        const int64_t b = t * (THREADS * BPT) + r * THREADS + threadIdx.x;
+        const int64_t b = b00 + r * THREADS;
         const int64_t b2 = b + THREADS;
         if (b2 < nblocks && ALIGNED && 4 * b2 + 4 <= n) {
-            const float4 o = b1_block<MODE>(philox_block(counter + (uint64_t)b, rk), cf, tab);
-            const float4 o2 = b1_block<MODE>(philox_block(counter + (uint64_t)b2, rk), cf, tab);
+            uint4 w, w2;
+            if (CARRY) {
+                w = philox_block(counter + (uint64_t)b, rk);
+                w2 = philox_block(counter + (uint64_t)b2, rk);
+            } else {
+                w = philox4x32_10(lo00 + (uint32_t)(r * THREADS), hi00, rk);
+                w2 = philox4x32_10(lo00 + (uint32_t)((r + 1) * THREADS), hi00, rk);
+            }
+            const float4 o = b1_block<MODE>(w, cf, tab);
+            const float4 o2 = b1_block<MODE>(w2, cf, tab);
             store4_aligned(out + 4 * b, o.x, o.y, o.z, o.w);
             store4_aligned(out + 4 * b2, o2.x, o2.y, o2.z, o2.w);
             continue;

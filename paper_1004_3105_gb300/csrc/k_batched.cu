@@ -5,23 +5,27 @@
 // and buffers the variable output of its vector Polar kernel (Sec. 4,
 // RANN3/RANN3B).  Here thousands of uneven streams share one grid:
 //   k_batched_prep (one CTA) validates the descriptors, turns each stream into
-//     work items and scans them, together with the Polar streams' tile status
-//     slots, into the workspace.  A B1 stream's items are its tiles; a Polar
-//     stream's are its expected number of tiles (primary items) plus one
-//     overflow item, placed after every stream's primary items, that runs
-//     whatever tiles the stream still needs, one after another;
-//   k_batched (persistent, one global work counter) pulls items in order,
-//     finds the stream in the item table the prep kernel wrote (one load) and
-//     runs a B1 tile or Polar tiles (look-back within the stream's own status
-//     words).
+//     work items and writes the item table: first every B1 stream's items
+//     (runs of its tiles), then every Polar stream's primary items (its
+//     expected number of tiles, one item each), then one overflow item per
+//     Polar stream that runs whatever tiles the stream still needs, one after
+//     another.  Entry i of the table names the stream and the tile of item i.
+//   k_batched (persistent, one global work counter) claims items in order,
+//     finds the stream in the item table (one load) and runs B1 tiles or
+//     Polar tiles (look-back within the stream's own status words).
+// The B1 items come first so that a CTA stages the sine/cosine table of the
+// accurate B1 path in shared memory once, in the space its Polar tiles use
+// later, and the batch ends on short Polar tiles rather than long B1 items.
+// The order of the items changes no output: every stream's values depend on
+// its own key, counter and length alone.
 // Items are handed out in increasing order, a CTA starts an item as soon as
 // it has claimed it, and a stream's tiles are claimed in increasing tile
 // order, so a Polar tile only waits on tiles already owned by running CTAs.
 // (Claiming the next item while the current one runs was measured: it lets
 // a claimed tile start up to a tile later than its successors, which then
-// wait in their look-back, and the whole batch ran twice as long.)  A Polar tile taken after its stream is
-// complete publishes a prefix of nitems and returns, so that any later tile's
-// look-back still ends.
+// wait in their look-back, and the whole batch ran twice as long.)  A Polar
+// tile taken after its stream is complete publishes a prefix of nitems and
+// returns, so that any later tile's look-back still ends.
 #include <algorithm>
 #include <climits>
 
@@ -46,11 +50,10 @@ int batched_config_count() { return kNumConfigs; }
 BatchedConfig batched_config(int id) { return kConfigs[id]; }
 int batched_default_config() { return 0; }
 
-// B1 tiles per B1 work item: a claim (an atomic and three dependent loads
-// while the CTA waits) is amortised over two tiles.  Measured on the
-// 4096-stream workload: 2 is 3.5% faster than 1 on all-B1 batches; 4 loses
-// on mixed batches to the longer tail of the last items.
-constexpr int kB1TilesPerItem = 2;
+// B1 tiles per B1 work item: a claim (an atomic and two dependent loads while
+// the CTA waits) is amortised over four tiles.  The B1 items all precede the
+// Polar items, so their length does not lengthen the tail of the batch.
+constexpr int kB1TilesPerItem = 4;
 
 __host__ __device__ inline int64_t b1_items(int64_t n, int64_t tile_blocks)
 {
@@ -60,10 +63,9 @@ __host__ __device__ inline int64_t b1_items(int64_t n, int64_t tile_blocks)
 
 // A Polar stream's primary tiles: the expected number of tiles its pairs
 // need at acceptance pi/4, ceil(nitems / (cand 0.7854)), at least one and at
-// most the tile budget.  They are its work items in the stream-ordered part
-// of the item space; whatever the stream still needs after them (a fraction
-// of a tile, at most a few) its overflow item takes, in the part of the item
-// space claimed after every primary tile.  Items for the whole tile budget
+// most the tile budget, one work item each; whatever the stream still needs
+// after them (a fraction of a tile, at most a few) its overflow item takes,
+// in the part of the item space claimed after every primary item.  Items for the whole tile budget
 // would spend the budget's margin (the 12-sigma excess and the extra tile)
 // on fully drawn tiles that are not needed, most of the work of a short
 // stream.
@@ -109,10 +111,10 @@ __host__ __device__ inline void stream_items(const nrng_stream_desc_t &d, int th
 
 size_t batched_workspace_bytes(const nrng_stream_desc_t *h_desc, int32_t k)
 {
-    // Sized for the configuration with the most status slots, so that any
-    // configuration (autotuned or pinned) fits the same workspace.
-    // Each configuration needs its tile status words and its item table
-    // (one 8-byte entry per primary item).
+    // Sized for the configuration with the most status slots and items, so
+    // that any configuration (autotuned or pinned) fits the same workspace.
+    // Each configuration needs its tile status words and its item table: one
+    // 8-byte entry per item, a Polar stream's overflow item included.
     size_t best = 0;
     for (int c = 0; c < kNumConfigs; ++c) {
         int64_t slots = 0, items = 0;
@@ -121,7 +123,7 @@ size_t batched_workspace_bytes(const nrng_stream_desc_t *h_desc, int32_t k)
             stream_items(h_desc[j], kConfigs[c].threads, kConfigs[c].blocks_per_thread, it, sl);
             if (it > 0) {
                 slots += sl;
-                items += it;
+                items += it + (h_desc[j].method == NRNG_POLAR ? 1 : 0);
             }
         }
         best = std::max(best, (size_t)(slots + items));
@@ -130,19 +132,42 @@ size_t batched_workspace_bytes(const nrng_stream_desc_t *h_desc, int32_t k)
 }
 
 // ------------------------------------------------------------ prep --------
-// One CTA: every thread takes a contiguous run of descriptors, sums their
-// items and status slots, and one block-wide exclusive scan places them.
-// Then every thread writes the item table entries of its streams: entry i
-// of the table is (stream, item of the stream) for primary item i, so that a
-// claim finds its stream with one load.  The table follows the tile status
+// One CTA: every thread takes a contiguous run of descriptors and counts
+// their B1 items, Polar primary items, Polar overflow items (one per Polar
+// stream with work) and status slots; one block-wide exclusive scan of the
+// four counts places them.  Then every thread writes the item table entries
+// of its streams: (stream, tile) for a B1 or primary item, (stream, -1 -
+// primary tiles) for an overflow item.  The table follows the tile status
 // words; its byte offset goes to the header (aux[2]).
 constexpr int kPrepThreads = 1024;
+constexpr int kPrepSums = 4;   // B1 items, Polar primary items, overflow items, slots
+
+// The four counts of one descriptor (all 0 for an invalid one, which is
+// recorded in *bad).
+__device__ __forceinline__ void prep_counts(const nrng_stream_desc_t &d, int threads, int bpt, int *bad,
+                                            long long (&c)[kPrepSums])
+{
+    int64_t items, slots;
+    stream_items(d, threads, bpt, items, slots);
+    c[0] = c[1] = c[2] = c[3] = 0;
+    if (items < 0) {
+        atomicMax(bad, items == -2 ? kStatusOverflow : kStatusInvalid);
+        return;
+    }
+    if (d.method == NRNG_B1) {
+        c[0] = items;
+    } else if (items > 0) {
+        c[1] = items;
+        c[2] = 1;
+        c[3] = slots;
+    }
+}
 
 __global__ void __launch_bounds__(kPrepThreads)
 k_batched_prep(BatchedParams bp, int threads, int bpt)
 {
-    __shared__ long long s_wi[kPrepThreads / 32], s_ws[kPrepThreads / 32];
-    __shared__ long long s_tot_items, s_tot_slots;
+    __shared__ long long s_w[kPrepSums][kPrepThreads / 32];
+    __shared__ long long s_tot[kPrepSums];
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_bad = 0;
@@ -150,95 +175,88 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
     const int32_t per = (bp.k + kPrepThreads - 1) / kPrepThreads;
     const int32_t j0 = tid * per;
     const int32_t j1 = (j0 + per < bp.k) ? j0 + per : bp.k;
-    // Each descriptor's items and slots are computed once (64-bit divisions
-    // and a square root) and kept for the second pass when they fit here.
+    // Each descriptor's counts are computed once (64-bit divisions and a
+    // square root) and kept for the second pass when they fit here.
     constexpr int kKeep = 4;
-    int64_t keep_items[kKeep], keep_slots[kKeep];
-    long long mi = 0, ms = 0;
+    long long keep[kKeep][kPrepSums];
+    long long m[kPrepSums] = {0, 0, 0, 0};
 #pragma unroll
-    for (int q = 0; q < kKeep; ++q) {   // unrolled: the kept values stay in registers
-        keep_items[q] = keep_slots[q] = 0;
-        const int32_t j = j0 + q;
-        if (j >= j1) continue;
-        int64_t items, slots;
-        stream_items(bp.desc[j], threads, bpt, items, slots);
-        if (items < 0) {
-            atomicMax(&s_bad, items == -2 ? kStatusOverflow : kStatusInvalid);
-            items = 0;
-            slots = 0;
-        }
-        keep_items[q] = items;
-        keep_slots[q] = slots;
-        mi += items;
-        ms += slots;
+    for (int r = 0; r < kKeep; ++r) {   // unrolled: the kept counts stay in registers
+#pragma unroll
+        for (int q = 0; q < kPrepSums; ++q) keep[r][q] = 0;
+        if (j0 + r < j1) prep_counts(bp.desc[j0 + r], threads, bpt, &s_bad, keep[r]);
+#pragma unroll
+        for (int q = 0; q < kPrepSums; ++q) m[q] += keep[r][q];
     }
-    for (int32_t j = j0 + kKeep; j < j1; ++j) {   // more than 4 descriptors a thread
-        int64_t items, slots;
-        stream_items(bp.desc[j], threads, bpt, items, slots);
-        if (items < 0) {
-            atomicMax(&s_bad, items == -2 ? kStatusOverflow : kStatusInvalid);
-            items = 0;
-            slots = 0;
-        }
-        mi += items;
-        ms += slots;
+    for (int32_t j = j0 + kKeep; j < j1; ++j) {   // more than four descriptors a thread
+        long long c[kPrepSums];
+        prep_counts(bp.desc[j], threads, bpt, &s_bad, c);
+#pragma unroll
+        for (int q = 0; q < kPrepSums; ++q) m[q] += c[q];
     }
-    long long ii = mi, is = ms;   // inclusive within the warp
+    long long inc[kPrepSums];   // inclusive within the warp
+#pragma unroll
+    for (int q = 0; q < kPrepSums; ++q) inc[q] = m[q];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const long long a = __shfl_up_sync(0xFFFFFFFFu, ii, o);
-        const long long b = __shfl_up_sync(0xFFFFFFFFu, is, o);
-        if (lane >= o) { ii += a; is += b; }
+#pragma unroll
+        for (int q = 0; q < kPrepSums; ++q) {
+            const long long a = __shfl_up_sync(0xFFFFFFFFu, inc[q], o);
+            if (lane >= o) inc[q] += a;
+        }
     }
-    if (lane == 31) { s_wi[warp] = ii; s_ws[warp] = is; }
+    if (lane == 31)
+#pragma unroll
+        for (int q = 0; q < kPrepSums; ++q) s_w[q][warp] = inc[q];
     __syncthreads();
     if (warp == 0) {
-        long long wi = s_wi[lane], ws = s_ws[lane];
-        const long long wi0 = wi, ws0 = ws;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long a = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-            const long long b = __shfl_up_sync(0xFFFFFFFFu, ws, o);
-            if (lane >= o) { wi += a; ws += b; }
-        }
-        s_wi[lane] = wi - wi0;   // exclusive warp offsets
-        s_ws[lane] = ws - ws0;
-        if (lane == 31) {
-            s_tot_items = wi;
-            s_tot_slots = ws;
+        for (int q = 0; q < kPrepSums; ++q) {
+            long long v = s_w[q][lane];
+            const long long v0 = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long a = __shfl_up_sync(0xFFFFFFFFu, v, o);
+                if (lane >= o) v += a;
+            }
+            s_w[q][lane] = v - v0;   // exclusive warp offsets
+            if (lane == 31) s_tot[q] = v;
         }
     }
     __syncthreads();
+    const long long n_b1 = s_tot[0], n_pp = s_tot[1], n_po = s_tot[2], n_slots = s_tot[3];
+    const long long n_items = n_b1 + n_pp + n_po;
     // the item table after the status words of every Polar stream; written
     // only when the workspace holds it (else the status word reports it)
-    const size_t table_off = batched_layout(bp.k).tile_status + (size_t)s_tot_slots * 8;
-    const bool table_fits = table_off + (size_t)s_tot_items * 8 <= bp.ws_bytes;
+    const size_t table_off = batched_layout(bp.k).tile_status + (size_t)n_slots * 8;
+    const bool table_fits = table_off + (size_t)n_items * 8 <= bp.ws_bytes;
     int2 *table = reinterpret_cast<int2 *>(reinterpret_cast<char *>(bp.hdr) + table_off);
-    long long ci = s_wi[warp] + ii - mi, cs = s_ws[warp] + is - ms;   // exclusive for this thread
+    long long x[kPrepSums];   // exclusive for this thread
 #pragma unroll
-    for (int q = 0; q < kKeep; ++q) {
-        const int32_t j = j0 + q;
-        if (j >= j1) continue;
-        bp.item_prefix[j] = ci;
+    for (int q = 0; q < kPrepSums; ++q) x[q] = s_w[q][warp] + inc[q] - m[q];
+    long long ib = x[0], ip = n_b1 + x[1], io = n_b1 + n_pp + x[2], cs = x[3];
+    auto place = [&](int32_t j, const long long (&c)[kPrepSums]) {
         bp.slot_base[j] = cs;
-        if (table_fits)
-            for (int64_t it = 0; it < keep_items[q]; ++it) table[ci + it] = make_int2(j, (int)it);
-        ci += keep_items[q];
-        cs += keep_slots[q];
-    }
+        if (table_fits) {
+            for (long long it = 0; it < c[0]; ++it) table[ib + it] = make_int2(j, (int)it);
+            for (long long it = 0; it < c[1]; ++it) table[ip + it] = make_int2(j, (int)it);
+            if (c[2]) table[io] = make_int2(j, -1 - (int)c[1]);
+        }
+        ib += c[0];
+        ip += c[1];
+        io += c[2];
+        cs += c[3];
+    };
+#pragma unroll
+    for (int r = 0; r < kKeep; ++r)
+        if (j0 + r < j1) place(j0 + r, keep[r]);
     for (int32_t j = j0 + kKeep; j < j1; ++j) {
-        int64_t items, slots;
-        stream_items(bp.desc[j], threads, bpt, items, slots);
-        if (items < 0) { items = 0; slots = 0; }
-        bp.item_prefix[j] = ci;
-        bp.slot_base[j] = cs;
-        if (table_fits)
-            for (int64_t it = 0; it < items; ++it) table[ci + it] = make_int2(j, (int)it);
-        ci += items;
-        cs += slots;
+        long long c[kPrepSums];
+        int ignored = 0;   // recorded in the first pass
+        prep_counts(bp.desc[j], threads, bpt, &ignored, c);
+        place(j, c);
     }
     if (tid == kPrepThreads - 1) {
-        bp.item_prefix[bp.k] = ci;
         int bad = s_bad;
         if (!bad && !table_fits) bad = kStatusWorkspace;
         if (bad) {
@@ -247,9 +265,8 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
             bp.hdr->aux[0] = 0;
             bp.hdr->aux[1] = 0;
         } else {
-            // primary items, then one overflow item per stream
-            bp.hdr->aux[0] = (unsigned long long)ci + (unsigned long long)bp.k;
-            bp.hdr->aux[1] = (unsigned long long)ci;
+            bp.hdr->aux[0] = (unsigned long long)n_items;
+            bp.hdr->aux[1] = (unsigned long long)n_b1;
             bp.hdr->aux[2] = (unsigned long long)table_off;
         }
     }
@@ -261,9 +278,17 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
 // for fewer where its tile's shared memory (with the 1 KB the runtime keeps
 // per CTA) admits fewer CTAs: the register budget follows from the smaller
 // count (128 x 16: six CTAs, up to 80 registers a thread; 128 x 12: eight, 64).
+// Shared memory of a batched CTA: a Polar tile's staging, or the sine/cosine
+// table of the accurate B1 path (16 KB) while the CTA runs B1 items.
+template <int THREADS, int BPT>
+union BatchedSmem {
+    RejSmem<THREADS / 32, BPT> rej;
+    float4 tab[1024];
+};
+
 template <int THREADS, int BPT, int MODE>
 struct BatchedOccupancy {
-    static constexpr int kSmemBlocks = (228 * 1024) / ((int)sizeof(RejSmem<THREADS / 32, BPT>) + 1024 + 256);
+    static constexpr int kSmemBlocks = (228 * 1024) / ((int)sizeof(BatchedSmem<THREADS, BPT>) + 1024 + 256);
     static constexpr int kThreadBlocks = 1024 / THREADS;
     static constexpr int kMin = kSmemBlocks < kThreadBlocks ? kSmemBlocks : kThreadBlocks;
     static constexpr int kMinBlocks = kMin > 0 ? kMin : 1;
@@ -279,12 +304,10 @@ struct BatchedWork {
 };
 
 // Claims the next item and resolves it to a stream and tile range (one
-// thread).  Items [0, primary) are the streams' primary items in stream
-// order, found in the item table with one load; item primary + j is stream
-// j's overflow item.
+// thread): one load of the item table names the stream and the tile, or, for
+// an overflow item, the stream's primary tiles (the first tile it may need).
 __device__ __forceinline__ void batched_claim(const BatchedParams &bp, const int2 *table,
-                                              unsigned long long total_items, unsigned long long primary, int cand,
-                                              BatchedWork &w)
+                                              unsigned long long total_items, int cand, BatchedWork &w)
 {
     // The error flag and the claim are issued together (one round trip, not
     // two); an item claimed after an error is dropped unprocessed.  This flag
@@ -293,30 +316,20 @@ __device__ __forceinline__ void batched_claim(const BatchedParams &bp, const int
     // (Stream completion is the per-stream flag, read after the claim.)
     const int failed = ld_relaxed_s32(&bp.hdr->done);
     const unsigned long long it = atomicAdd(&bp.hdr->tile_counter, 1ull);
-    const long long item = (failed == 0 && it < total_items) ? (long long)it : -1;
-    if (item < 0) {
+    if (failed != 0 || it >= total_items) {
         w.stream = -1;
         return;
     }
-    int j;
-    if ((unsigned long long)item < primary) {
-        const int2 e = table[item];
-        j = e.x;
-        w.t0 = e.y;
-        w.t1 = w.t0 + 1;
-        w.overflow = 0;
-    } else {
-        j = (int)(item - (long long)primary);
-        w.t0 = bp.item_prefix[j + 1] - bp.item_prefix[j];   // the stream's primary tiles
-        w.overflow = 1;
-    }
+    const int2 e = table[it];
+    const int j = e.x;
     // The descriptor and the stream's completion flag are loaded together
     // (B1 streams' flags stay 0).
     const int stream_done = ld_relaxed_s32(bp.stream_done + j);
     w.d = bp.desc[j];
-    const bool polar = (w.d.method == NRNG_POLAR);
-    if (w.overflow) w.t1 = polar ? polar_tiles_for(w.d.n, cand) : w.t0;   // B1 has no overflow
-    w.skip = polar ? stream_done : 0;
+    w.overflow = e.y < 0;
+    w.t0 = w.overflow ? -1 - (long long)e.y : e.y;
+    w.t1 = w.overflow ? polar_tiles_for(w.d.n, cand) : w.t0 + 1;
+    w.skip = (w.d.method == NRNG_POLAR) ? stream_done : 0;
     w.stream = j;
 }
 
@@ -325,16 +338,16 @@ __global__ void __launch_bounds__(THREADS, (BatchedOccupancy<THREADS, BPT, MODE>
 k_batched(BatchedParams bp)
 {
     constexpr int kCand = 2 * THREADS * BPT;
-    __shared__ RejSmem<THREADS / 32, BPT> sm;
+    __shared__ BatchedSmem<THREADS, BPT> sm;
     __shared__ BatchedWork s_work;
     __shared__ int s_done;
 
     const unsigned long long total_items = bp.hdr->aux[0];
-    const unsigned long long primary = bp.hdr->aux[1];
     const int2 *table = reinterpret_cast<const int2 *>(reinterpret_cast<const char *>(bp.hdr) + bp.hdr->aux[2]);
     char *out_base = static_cast<char *>(bp.out);
+    bool tab_staged = false;   // sm.tab holds the sine/cosine table
     for (;;) {
-        if (threadIdx.x == 0) batched_claim(bp, table, total_items, primary, kCand, s_work);
+        if (threadIdx.x == 0) batched_claim(bp, table, total_items, kCand, s_work);
         __syncthreads();
         const int j = s_work.stream;
         if (j < 0) break;
@@ -353,23 +366,31 @@ k_batched(BatchedParams bp)
             constexpr int64_t kSpan = (int64_t)THREADS * BPT * kB1TilesPerItem;
             const uint64_t first = d.counter + (uint64_t)(t0 * kSpan);
             const bool carry_free = (uint64_t)(uint32_t)first + (uint64_t)kSpan <= (uint64_t(1) << 32);
-            if (overflow) {
-                // B1 streams have no overflow tiles
-            } else if (((uintptr_t)out % (4 * sizeof(T))) == 0) {
+            const float4 *tab = kSinCos1024;
+            if (MODE == kModeAccurate) {
+                if (!tab_staged) {   // the CTA's first B1 item (the items before were none or Polar)
+                    for (int i = threadIdx.x; i < 1024; i += THREADS) sm.tab[i] = kSinCos1024[i];
+                    __syncthreads();
+                    tab_staged = true;
+                }
+                tab = sm.tab;
+            }
+            if (((uintptr_t)out % (4 * sizeof(T))) == 0) {
                 if (carry_free)
                     for (int q = 0; q < kB1TilesPerItem; ++q)
-                        b1_tile<THREADS, BPT, MODE, T, true, false>(out, d.n, cf, kSinCos1024, rk, d.counter,
+                        b1_tile<THREADS, BPT, MODE, T, true, false>(out, d.n, cf, tab, rk, d.counter,
                                                                     t0 * kB1TilesPerItem + q);
                 else
                     for (int q = 0; q < kB1TilesPerItem; ++q)
-                        b1_tile<THREADS, BPT, MODE, T, true, true>(out, d.n, cf, kSinCos1024, rk, d.counter,
+                        b1_tile<THREADS, BPT, MODE, T, true, true>(out, d.n, cf, tab, rk, d.counter,
                                                                    t0 * kB1TilesPerItem + q);
             } else {
                 for (int q = 0; q < kB1TilesPerItem; ++q)
-                    b1_tile<THREADS, BPT, MODE, T, false, true>(out, d.n, cf, kSinCos1024, rk, d.counter,
+                    b1_tile<THREADS, BPT, MODE, T, false, true>(out, d.n, cf, tab, rk, d.counter,
                                                                 t0 * kB1TilesPerItem + q);
             }
         } else if (!(overflow && skip)) {
+            tab_staged = false;   // the Polar tile's staging overwrites the table
             const RadiusCoef cf = radius_coef(d.mu, d.sigma);
             PolarStream ps;
             ps.n = d.n;
@@ -395,10 +416,10 @@ k_batched(BatchedParams bp)
                     // Stream complete: every later tile's prefix is >= nitems.
                     if (threadIdx.x == 0) st_relaxed(ps.status + t, kFlagPrefix | (unsigned long long)ps.nitems);
                 } else if (aligned) {
-                    ok = reject_tile<PolarPolicy<MODE>, THREADS / 32, BPT, T, true, true>(sm, out, ps, rk, cf, t, bp.hdr,
+                    ok = reject_tile<PolarPolicy<MODE>, THREADS / 32, BPT, T, true, true>(sm.rej, out, ps, rk, cf, t, bp.hdr,
                                                                                          bp.spin_limit_ns);
                 } else {
-                    ok = reject_tile<PolarPolicy<MODE>, THREADS / 32, BPT, T, false, true>(sm, out, ps, rk, cf, t, bp.hdr,
+                    ok = reject_tile<PolarPolicy<MODE>, THREADS / 32, BPT, T, false, true>(sm.rej, out, ps, rk, cf, t, bp.hdr,
                                                                                           bp.spin_limit_ns);
                 }
                 __syncthreads();
@@ -454,7 +475,6 @@ cudaError_t launch_batched(void *out, const nrng_stream_desc_t *desc, int32_t k,
     bp.desc = desc;
     bp.k = k;
     bp.hdr = reinterpret_cast<WsHeader *>(w);
-    bp.item_prefix = reinterpret_cast<int64_t *>(w + L.item_prefix);
     bp.slot_base = reinterpret_cast<int64_t *>(w + L.slot_base);
     bp.stream_done = reinterpret_cast<int *>(w + L.stream_done);
     bp.tile_status = reinterpret_cast<unsigned long long *>(w + L.tile_status);

@@ -140,9 +140,8 @@ struct BatchedConfig {
 };
 
 // Workspace of a batched call: header, then per-stream tables, then one tile
-// status word per Polar tile of every Polar stream.
+// status word per Polar tile of every Polar stream, then the item table.
 struct BatchedLayout {
-    size_t item_prefix;   // int64[k + 1]: first work item of each stream
     size_t slot_base;     // int64[k]: first tile status word of each Polar stream
     size_t stream_done;   // int32[k]: set once a Polar stream has all its pairs
     size_t tile_status;   // uint64[slots]
@@ -150,8 +149,7 @@ struct BatchedLayout {
 __host__ __device__ inline BatchedLayout batched_layout(int32_t k)
 {
     BatchedLayout L;
-    L.item_prefix = sizeof(WsHeader);
-    L.slot_base = L.item_prefix + (size_t)(k + 1) * 8;
+    L.slot_base = sizeof(WsHeader);
     L.stream_done = L.slot_base + (size_t)k * 8;
     L.tile_status = (L.stream_done + (size_t)k * 4 + 255) / 256 * 256;
     return L;
@@ -162,7 +160,6 @@ struct BatchedParams {
     const nrng_stream_desc_t *desc;
     int32_t k;
     WsHeader *hdr;
-    int64_t *item_prefix;
     int64_t *slot_base;
     int *stream_done;
     unsigned long long *tile_status;

@@ -25,6 +25,8 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=list(DT))
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--streams", type=int, default=1024, help="batched: number of streams")
+    ap.add_argument("--methods", default="mixed", choices=["mixed", "b1", "polar"],
+                    help="batched: the streams' methods")
     a = ap.parse_args()
     nr.load()
     dev = torch.device("cuda", 0)
@@ -41,7 +43,7 @@ def main():
             else:
                 nr.nrng_polar(out, 0.0, 1.0, W.KEY_MAIN, 0, ws, a.mode)
     elif a.kernel == "batched":
-        wl = W.batched_workload(k=a.streams, methods="mixed", align=4)
+        wl = W.batched_workload(k=a.streams, methods=a.methods, align=4)
         desc = nr.stream_descriptors(wl.offset, wl.n, wl.mu, wl.sigma, wl.key, wl.counter, wl.method)
         d_desc = nr.descriptors_to_device(desc, dev)
         out = torch.empty(wl.total, dtype=dt, device=dev)

@@ -158,11 +158,11 @@ def test_batched_workspace_size(lib):
     b = ctypes.c_size_t(0)
     assert lib.nrng_batched_workspace_size(d.ctypes.data_as(ctypes.c_void_p), len(d), ctypes.byref(b)) == _lib.OK
     k = len(d)
-    fixed = (64 + (k + 1) * 8 + k * 8 + k * 4 + 255) // 256 * 256
+    fixed = (64 + k * 8 + k * 4 + 255) // 256 * 256
     # most status slots plus item-table entries over the configurations (one
     # 8-byte entry each): a Polar stream's slots are its tile budget and its
-    # items its expected tiles at acceptance pi/4; a B1 stream has no slots and
-    # one item per two tiles
+    # items its expected tiles at acceptance pi/4 plus one overflow item; a B1
+    # stream has no slots and one item per four tiles
     worst = 0
     for threads, bpt in [(128, 16), (128, 12), (128, 8), (256, 8), (128, 4), (256, 4)]:
         cand = 2 * threads * bpt
@@ -171,13 +171,13 @@ def test_batched_workspace_size(lib):
             if n == 0:
                 continue
             if m == 0:
-                s += (((n + 3) // 4) + 2 * threads * bpt - 1) // (2 * threads * bpt)
+                s += (((n + 3) // 4) + 4 * threads * bpt - 1) // (4 * threads * bpt)
                 continue
             npairs = (n + 1) // 2
             need = npairs + 12 * (int(np.sqrt(npairs)) + 1) + 16
             budget = (need * 100 + cand * 78 - 1) // (cand * 78) + 1
             primary = min(max(1, (npairs * 10000 + cand * 7854 - 1) // (cand * 7854)), budget)
-            s += budget + primary
+            s += budget + primary + 1
         worst = max(worst, s)
     assert b.value == fixed + 8 * worst
     big = _desc([100, 2 ** 60 + 1], [0, 0])   # a stream beyond the element cap

@@ -5,6 +5,9 @@ Method B3 (Sec. 3), Method P2 (Sec. 4, step 4a) and the Ratio method R
 within the fast-path tolerance (B2, B3, P2: polynomial approximations) or the
 accurate one (R: one division); every dtype, odd and tiny n, unaligned
 outputs; a full-size sample at 2^28; normality."""
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -159,6 +162,52 @@ def test_ratio_full_size_accept_order_and_sample():
     idx = W.sample_indices(n, 1 << 16)
     assert_close(out[torch.from_numpy(idx).cuda()], oracle.ratio_at(cand[idx], 0.0, 1.0, W.KEY_MAIN, 0),
                  0.0, 1.0, "accurate", "R 2^28 sampled")
+
+
+def _ratio_fp64_decisions(ncand, key, counter, chunk=1 << 24):
+    """How many of candidates 0 .. ncand-1 fall inside the float screen's
+    margin, where the kernel decides Algorithm R's step 3 in FP64: the
+    screen's float32 arithmetic emulated in numpy, with a correctly rounded
+    log2 in place of the hardware one (so a candidate at the very edge of the
+    margin may count differently)."""
+    f = np.float32
+    total = 0
+    for c0 in range(0, ncand, 2 * chunk):
+        nb = min(chunk, (ncand - c0 + 1) // 2)
+        w = oracle.philox_blocks(nb, key, counter + c0 // 2).astype(np.uint32)
+        for h in (0, 1):
+            wu, wv = w[:, 2 * h], w[:, 2 * h + 1]
+            k = (wu >> np.uint32(8)).astype(np.int64)
+            a = (wv >> np.uint32(8)).astype(np.int64) - (1 << 23)
+            fa, fb = a.astype(f), ((1 << 24) - k).astype(f)
+            lhs = (f(2.0) * fa) * fa
+            u = k.astype(f) * f(2.0 ** -24)
+            series = u * (f(2.0) + u * (f(1.0) + u * (f(0.66666669) + u * (f(0.5) + u * f(0.4)))))
+            logv = np.log2((k.astype(f) * f(-(2.0 ** -24)) + f(1.0)).astype(f)).astype(f) * f(-1.38629436)
+            m2l = np.where(u < f(0.0625), series, logv).astype(f)
+            rhs = ((f(1.35914091) * fb) * fb) * m2l
+            margin = f(1e-5) * (lhs + rhs) + f(1.0)
+            inband = ~((rhs - lhs) > margin) & ~((lhs - rhs) > margin)
+            idx = c0 + 2 * np.arange(nb) + h
+            total += int(np.count_nonzero(inband & (idx < ncand)))
+    return total
+
+
+def test_ratio_fp64_decisions_at_full_size():
+    """Algorithm R's accept test is the only FP64 arithmetic on the GPU: it
+    runs for candidates inside the float screen's margin.  At N = 2^28 (the
+    candidates a full-size call consumes) this counts them and prints the
+    fraction; it must stay a small fraction of the candidates."""
+    n = 1 << 28
+    _, cand, _ = run_ratio(n, 0.0, 1.0, W.KEY_MAIN, 0)
+    ncand = int(cand[-1]) + 1
+    cnt = _ratio_fp64_decisions(ncand, W.KEY_MAIN, 0)
+    print(f"R at N = 2^28: {ncand} candidates, {cnt} decided in FP64 ({cnt / ncand:.3e})")
+    path = os.environ.get("NRNG_ERROR_TABLE")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps({"variant": "ratio fp64 decisions", "candidates": ncand, "fp64": cnt}) + "\n")
+    assert 0 < cnt < ncand // 1000
 
 
 def test_ratio_continuation():

@@ -18,14 +18,16 @@
 // later, and the batch ends on short Polar tiles rather than long B1 items.
 // The order of the items changes no output: every stream's values depend on
 // its own key, counter and length alone.
-// Items are handed out in increasing order, a CTA starts an item as soon as
-// it has claimed it, and a stream's tiles are claimed in increasing tile
-// order, so a Polar tile only waits on tiles already owned by running CTAs.
-// (Claiming the next item while the current one runs was measured: it lets
-// a claimed tile start up to a tile later than its successors, which then
-// wait in their look-back, and the whole batch ran twice as long.)  A Polar
-// tile taken after its stream is complete publishes a prefix of nitems and
-// returns, so that any later tile's look-back still ends.
+// Items are handed out in increasing order and a stream's tiles are claimed
+// in increasing tile order; a CTA starts a Polar item as soon as it has
+// claimed it, or, when it claimed the item ahead while running a B1 item, as
+// soon as that B1 item ends, so a Polar tile only waits on tiles owned by
+// CTAs that are running or about to start them.  (Claiming ahead while a
+// Polar tile runs was measured: it lets a claimed tile start up to a tile
+// later than its successors, which then wait in their look-back, and the
+// whole batch ran twice as long.)  A Polar tile taken after its stream is
+// complete publishes a prefix of nitems and returns, so that any later
+// tile's look-back still ends.
 #include <algorithm>
 #include <climits>
 
@@ -303,19 +305,17 @@ struct BatchedWork {
     int overflow;   // the stream's overflow item
 };
 
-// Claims the next item and resolves it to a stream and tile range (one
-// thread): one load of the item table names the stream and the tile, or, for
-// an overflow item, the stream's primary tiles (the first tile it may need).
-__device__ __forceinline__ void batched_claim(const BatchedParams &bp, const int2 *table,
-                                              unsigned long long total_items, int cand, BatchedWork &w)
+// Resolves claimed item `it` to a stream and tile range (one thread): one
+// load of the item table names the stream and the tile, or, for an overflow
+// item, the stream's primary tiles (the first tile it may need).
+__device__ __forceinline__ void batched_resolve(const BatchedParams &bp, const int2 *table, unsigned long long it,
+                                                unsigned long long total_items, int cand, BatchedWork &w)
 {
-    // The error flag and the claim are issued together (one round trip, not
-    // two); an item claimed after an error is dropped unprocessed.  This flag
+    // An item claimed after an error is dropped unprocessed.  The error flag
     // is set only on an error, and every look-back gives up as soon as the
     // status word is set, so a dropped item never holds up a successor.
-    // (Stream completion is the per-stream flag, read after the claim.)
+    // (Stream completion is the per-stream flag, read below.)
     const int failed = ld_relaxed_s32(&bp.hdr->done);
-    const unsigned long long it = atomicAdd(&bp.hdr->tile_counter, 1ull);
     if (failed != 0 || it >= total_items) {
         w.stream = -1;
         return;
@@ -343,11 +343,24 @@ k_batched(BatchedParams bp)
     __shared__ int s_done;
 
     const unsigned long long total_items = bp.hdr->aux[0];
+    const unsigned long long b1_items_end = bp.hdr->aux[1];
     const int2 *table = reinterpret_cast<const int2 *>(reinterpret_cast<const char *>(bp.hdr) + bp.hdr->aux[2]);
     char *out_base = static_cast<char *>(bp.out);
     bool tab_staged = false;   // sm.tab holds the sine/cosine table
+    // Thread 0's claims: the current item, and the next one when it was
+    // claimed ahead (kNone: not yet).  A CTA claims ahead only while it runs a
+    // B1 item, which waits on nothing, so a claimed-ahead Polar tile is
+    // started once that item ends and its successors' look-backs still end;
+    // and only far from the end of the B1 items, so that hardly any Polar tile
+    // is claimed ahead (a late tile holds up its stream's later tiles).
+    constexpr unsigned long long kNone = ~0ull;
+    unsigned long long cur = kNone, ahead = kNone;
     for (;;) {
-        if (threadIdx.x == 0) batched_claim(bp, table, total_items, kCand, s_work);
+        if (threadIdx.x == 0) {
+            cur = (ahead != kNone) ? ahead : atomicAdd(&bp.hdr->tile_counter, 1ull);
+            ahead = kNone;
+            batched_resolve(bp, table, cur, total_items, kCand, s_work);
+        }
         __syncthreads();
         const int j = s_work.stream;
         if (j < 0) break;
@@ -366,6 +379,8 @@ k_batched(BatchedParams bp)
             constexpr int64_t kSpan = (int64_t)THREADS * BPT * kB1TilesPerItem;
             const uint64_t first = d.counter + (uint64_t)(t0 * kSpan);
             const bool carry_free = (uint64_t)(uint32_t)first + (uint64_t)kSpan <= (uint64_t(1) << 32);
+            if (threadIdx.x == 0 && cur + 2 * (unsigned long long)gridDim.x < b1_items_end)
+                ahead = atomicAdd(&bp.hdr->tile_counter, 1ull);   // read at the next claim
             const float4 *tab = kSinCos1024;
             if (MODE == kModeAccurate) {
                 if (!tab_staged) {   // the CTA's first B1 item (the items before were none or Polar)

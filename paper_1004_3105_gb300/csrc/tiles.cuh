@@ -15,10 +15,24 @@ template <int THREADS, int BPT, int MODE, typename T, bool ALIGNED, bool CARRY, 
 __device__ __forceinline__ void b1_tile(T *__restrict__ out, int64_t n, const RadiusCoef &cf, const float4 *tab,
                                         const Key &rk, uint64_t counter, int64_t t)
 {
+    static_assert(BPT % 2 == 0, "rows are taken in pairs");
     const int64_t nblocks = (n + 3) / 4;
     const int64_t b00 = t * (THREADS * BPT) + threadIdx.x;
     const uint64_t c00 = counter + (uint64_t)b00;
     const uint32_t lo00 = (uint32_t)c00, hi00 = (uint32_t)(c00 >> 32);
+    if (ALIGNED && !CARRY && 4 * (t + 1) * (THREADS * BPT) <= n) {
+        // The whole tile in range: no bounds checks, a 32-bit counter word
+        // and one output pointer stepped per pair of rows.
+        T *o = out + 4 * b00;
+        uint32_t lo = lo00;
+        for (int r = 0; r < BPT; r += 2, lo += 2 * THREADS, o += 8 * THREADS) {
+            const float4 v = b1_block<MODE>(philox4x32_10(lo, hi00, rk), cf, tab);
+            const float4 v2 = b1_block<MODE>(philox4x32_10(lo + THREADS, hi00, rk), cf, tab);
+            store4_aligned(o, v.x, v.y, v.z, v.w);
+            store4_aligned(o + 4 * THREADS, v2.x, v2.y, v2.z, v2.w);
+        }
+        return;
+    }
     // Two rows per step when both are in range: the two Philox chains are
     // independent and fill each other's multiply stalls.
     for (int r = 0; r < BPT; r += 2) {

@@ -19,15 +19,15 @@
 // The order of the items changes no output: every stream's values depend on
 // its own key, counter and length alone.
 // Items are handed out in increasing order and a stream's tiles are claimed
-// in increasing tile order; a CTA starts a Polar item as soon as it has
-// claimed it, or, when it claimed the item ahead while running a B1 item, as
-// soon as that B1 item ends, so a Polar tile only waits on tiles owned by
-// CTAs that are running or about to start them.  (Claiming ahead while a
-// Polar tile runs was measured: it lets a claimed tile start up to a tile
-// later than its successors, which then wait in their look-back, and the
-// whole batch ran twice as long.)  A Polar tile taken after its stream is
-// complete publishes a prefix of nitems and returns, so that any later
-// tile's look-back still ends.
+// in increasing tile order.  A CTA claims its next item ahead only while the
+// rest of its current item waits on nothing (a B1 item, or a Polar tile's
+// copy-out once its prefix is known), so a Polar tile only waits on tiles
+// owned by CTAs that are running them or about to start them.  (Claiming
+// ahead at the start of a Polar tile was measured: it lets a claimed tile
+// start up to a tile later than its successors, which then wait in their
+// look-back, and the whole batch ran twice as long.)  A Polar tile taken
+// after its stream is complete publishes a prefix of nitems and returns, so
+// that any later tile's look-back still ends.
 #include <algorithm>
 #include <climits>
 
@@ -259,6 +259,7 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
         place(j, c);
     }
     if (tid == kPrepThreads - 1) {
+        bp.slot_base[bp.k] = cs;
         int bad = s_bad;
         if (!bad && !table_fits) bad = kStatusWorkspace;
         if (bad) {
@@ -300,6 +301,7 @@ struct BatchedOccupancy {
 struct BatchedWork {
     nrng_stream_desc_t d;
     long long t0, t1;
+    long long slot0, tiles_max;   // a Polar stream's first status word and tile budget
     int stream;
     int skip;       // Polar stream complete when claimed
     int overflow;   // the stream's overflow item
@@ -307,9 +309,10 @@ struct BatchedWork {
 
 // Resolves claimed item `it` to a stream and tile range (one thread): one
 // load of the item table names the stream and the tile, or, for an overflow
-// item, the stream's primary tiles (the first tile it may need).
+// item, the stream's primary tiles (the first tile it may need); an overflow
+// item runs up to the stream's tile budget.
 __device__ __forceinline__ void batched_resolve(const BatchedParams &bp, const int2 *table, unsigned long long it,
-                                                unsigned long long total_items, int cand, BatchedWork &w)
+                                                unsigned long long total_items, BatchedWork &w)
 {
     // An item claimed after an error is dropped unprocessed.  The error flag
     // is set only on an error, and every look-back gives up as soon as the
@@ -322,16 +325,32 @@ __device__ __forceinline__ void batched_resolve(const BatchedParams &bp, const i
     }
     const int2 e = table[it];
     const int j = e.x;
-    // The descriptor and the stream's completion flag are loaded together
-    // (B1 streams' flags stay 0).
+    // The descriptor, the stream's status words and its completion flag are
+    // loaded together (B1 streams have no status words, their flags stay 0).
     const int stream_done = ld_relaxed_s32(bp.stream_done + j);
     w.d = bp.desc[j];
+    w.slot0 = bp.slot_base[j];
+    w.tiles_max = bp.slot_base[j + 1] - w.slot0;
     w.overflow = e.y < 0;
     w.t0 = w.overflow ? -1 - (long long)e.y : e.y;
-    w.t1 = w.overflow ? polar_tiles_for(w.d.n, cand) : w.t0 + 1;
+    w.t1 = w.overflow ? w.tiles_max : w.t0 + 1;
     w.skip = (w.d.method == NRNG_POLAR) ? stream_done : 0;
     w.stream = j;
 }
+
+// A Polar primary item claims the next item once its tile's prefix is known:
+// only the copy-out is left, so the claimed item starts a copy-out later than
+// a claim made after the item (an overflow item, which may run more tiles,
+// does not claim ahead).
+struct ClaimAhead {
+    unsigned long long *counter;
+    unsigned long long *ahead;
+    bool on;
+    __device__ __forceinline__ void operator()() const
+    {
+        if (on) *ahead = atomicAdd(counter, 1ull);
+    }
+};
 
 template <int THREADS, int BPT, int MODE, typename T>
 __global__ void __launch_bounds__(THREADS, (BatchedOccupancy<THREADS, BPT, MODE>::kMinBlocks))
@@ -348,18 +367,20 @@ k_batched(BatchedParams bp)
     char *out_base = static_cast<char *>(bp.out);
     bool tab_staged = false;   // sm.tab holds the sine/cosine table
     // Thread 0's claims: the current item, and the next one when it was
-    // claimed ahead (kNone: not yet).  A CTA claims ahead only while it runs a
-    // B1 item, which waits on nothing, so a claimed-ahead Polar tile is
-    // started once that item ends and its successors' look-backs still end;
-    // and only far from the end of the B1 items, so that hardly any Polar tile
-    // is claimed ahead (a late tile holds up its stream's later tiles).
+    // claimed ahead (kNone: not yet).  A CTA claims ahead while it runs a B1
+    // item, which waits on nothing, or once its Polar tile has its prefix
+    // (only the copy-out left, which waits on nothing), so a claimed-ahead
+    // Polar tile is started after a bounded time and its successors'
+    // look-backs still end.  During a B1 item it claims ahead only far from
+    // the end of the B1 items, so that hardly any Polar tile waits a whole B1
+    // item (a late tile holds up its stream's later tiles).
     constexpr unsigned long long kNone = ~0ull;
     unsigned long long cur = kNone, ahead = kNone;
     for (;;) {
         if (threadIdx.x == 0) {
             cur = (ahead != kNone) ? ahead : atomicAdd(&bp.hdr->tile_counter, 1ull);
             ahead = kNone;
-            batched_resolve(bp, table, cur, total_items, kCand, s_work);
+            batched_resolve(bp, table, cur, total_items, s_work);
         }
         __syncthreads();
         const int j = s_work.stream;
@@ -411,8 +432,8 @@ k_batched(BatchedParams bp)
             ps.n = d.n;
             ps.nitems = (d.n + 1) / 2;
             ps.counter = d.counter;
-            ps.status = bp.tile_status + bp.slot_base[j];
-            ps.tiles_max = polar_tiles_for(d.n, kCand);
+            ps.status = bp.tile_status + s_work.slot0;
+            ps.tiles_max = s_work.tiles_max;
             ps.done = bp.stream_done + j;
             ps.next_counter = nullptr;
             ps.pair_cand = nullptr;
@@ -431,11 +452,11 @@ k_batched(BatchedParams bp)
                     // Stream complete: every later tile's prefix is >= nitems.
                     if (threadIdx.x == 0) st_relaxed(ps.status + t, kFlagPrefix | (unsigned long long)ps.nitems);
                 } else if (aligned) {
-                    ok = reject_tile<PolarPolicy<MODE>, THREADS / 32, BPT, T, true, true>(sm.rej, out, ps, rk, cf, t, bp.hdr,
-                                                                                         bp.spin_limit_ns);
+                    ok = reject_tile<PolarPolicy<MODE>, THREADS / 32, BPT, T, true, true, RoundKeys, false>(
+                        sm.rej, out, ps, rk, cf, t, bp.hdr, bp.spin_limit_ns, 0, ClaimAhead{&bp.hdr->tile_counter, &ahead, !overflow});
                 } else {
-                    ok = reject_tile<PolarPolicy<MODE>, THREADS / 32, BPT, T, false, true>(sm.rej, out, ps, rk, cf, t, bp.hdr,
-                                                                                          bp.spin_limit_ns);
+                    ok = reject_tile<PolarPolicy<MODE>, THREADS / 32, BPT, T, false, true, RoundKeys, false>(
+                        sm.rej, out, ps, rk, cf, t, bp.hdr, bp.spin_limit_ns, 0, ClaimAhead{&bp.hdr->tile_counter, &ahead, !overflow});
                 }
                 __syncthreads();
                 if (!ok) break;

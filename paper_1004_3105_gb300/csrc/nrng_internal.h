@@ -142,7 +142,8 @@ struct BatchedConfig {
 // Workspace of a batched call: header, then per-stream tables, then one tile
 // status word per Polar tile of every Polar stream, then the item table.
 struct BatchedLayout {
-    size_t slot_base;     // int64[k]: first tile status word of each Polar stream
+    size_t slot_base;     // int64[k + 1]: first tile status word of each stream (the
+                          // difference of neighbours: a Polar stream's tile budget)
     size_t stream_done;   // int32[k]: set once a Polar stream has all its pairs
     size_t tile_status;   // uint64[slots]
 };
@@ -150,7 +151,7 @@ __host__ __device__ inline BatchedLayout batched_layout(int32_t k)
 {
     BatchedLayout L;
     L.slot_base = sizeof(WsHeader);
-    L.stream_done = L.slot_base + (size_t)k * 8;
+    L.stream_done = L.slot_base + (size_t)(k + 1) * 8;
     L.tile_status = (L.stream_done + (size_t)k * 4 + 255) / 256 * 256;
     return L;
 }

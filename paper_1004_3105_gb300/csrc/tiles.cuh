@@ -232,10 +232,18 @@ __device__ __forceinline__ int tile_candidate(const RejSmem<NW, R> &sm, int warp
 // KNOWN_PREFIX the tile's exclusive prefix is given (from a count pass and a
 // scan): nothing is published and nothing is awaited.  With CARRY false the
 // low counter word of the tile's blocks does not wrap (the caller checks).
-template <class Policy, int NW, int R, typename T, bool ALIGNED, bool CARRY, typename Key, bool KNOWN_PREFIX = false>
+// on_prefix() runs on thread 0 once the tile's prefix is known (after the
+// look-back, before the copy-out), when the look-back succeeded.
+struct NoPrefixHook {
+    __device__ void operator()() const {}
+};
+
+template <class Policy, int NW, int R, typename T, bool ALIGNED, bool CARRY, typename Key, bool KNOWN_PREFIX = false,
+          class OnPrefix = NoPrefixHook>
 __device__ __forceinline__ bool reject_tile(RejSmem<NW, R> &sm, T *__restrict__ out, const PolarStream &ps,
                                             const Key &rk, const RadiusCoef &cf, int64_t t, WsHeader *hdr,
-                                            unsigned long long limit_ns, long long known_prefix = 0)
+                                            unsigned long long limit_ns, long long known_prefix = 0,
+                                            OnPrefix on_prefix = OnPrefix())
 {
     constexpr int kBPT = NW * R * 32;   // Philox blocks of a tile
     constexpr int kCand = 2 * kBPT;
@@ -319,6 +327,7 @@ __device__ __forceinline__ bool reject_tile(RejSmem<NW, R> &sm, T *__restrict__ 
                 if (P < ps.nitems && P + total >= ps.nitems) st_relaxed_s32(ps.done, 1);
                 if (t == ps.tiles_max - 1 && P + total < ps.nitems) raise_error(hdr, kStatusExhausted);
             }
+            if (P >= 0) on_prefix();
         }
     }
     __syncthreads();

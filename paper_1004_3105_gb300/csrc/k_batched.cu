@@ -4,8 +4,9 @@
 // The paper amortises the cost of a call by returning whole arrays (Sec. 3)
 // and buffers the variable output of its vector Polar kernel (Sec. 4,
 // RANN3/RANN3B).  Here thousands of uneven streams share one grid:
-//   k_batched_prep (one CTA) validates the descriptors, turns each stream into
-//     work items and writes the item table: first every B1 stream's items
+//   k_batched_count, k_batched_scan and k_batched_fill validate the
+//     descriptors, turn each stream into work items and write the item table
+//     (a thread, one CTA and a warp per stream): first every B1 stream's items
 //     (runs of its tiles), then every Polar stream's primary items (its
 //     expected number of tiles, one item each), then one overflow item per
 //     Polar stream that runs whatever tiles the stream still needs, one after
@@ -71,11 +72,10 @@ __host__ __device__ inline int64_t b1_items(int64_t n, int64_t tile_blocks)
 // would spend the budget's margin (the 12-sigma excess and the extra tile)
 // on fully drawn tiles that are not needed, most of the work of a short
 // stream.
-__host__ __device__ inline int64_t polar_primary_tiles(int64_t n, int64_t cand)
+__host__ __device__ inline int64_t polar_primary_tiles(int64_t n, int64_t cand, int64_t budget)
 {
     const int64_t nitems = (n + 1) / 2;
     const int64_t t = (nitems * 10000 + cand * 7854 - 1) / (cand * 7854);
-    const int64_t budget = polar_tiles_for(n, cand);
     return t < 1 ? 1 : (t > budget ? budget : t);
 }
 
@@ -100,7 +100,7 @@ __host__ __device__ inline void stream_items(const nrng_stream_desc_t &d, int th
         if (d.counter > ULLONG_MAX - (blocks - 1)) items = -2;
     } else {
         slots = polar_tiles_for(d.n, 2 * tile_blocks);
-        items = polar_primary_tiles(d.n, 2 * tile_blocks);
+        items = polar_primary_tiles(d.n, 2 * tile_blocks, slots);
         const uint64_t blocks = (uint64_t)(slots * tile_blocks);
         if (d.counter > ULLONG_MAX - (blocks - 1)) items = -2;
     }
@@ -134,86 +134,104 @@ size_t batched_workspace_bytes(const nrng_stream_desc_t *h_desc, int32_t k)
 }
 
 // ------------------------------------------------------------ prep --------
-// One CTA: every thread takes a contiguous run of descriptors and counts
-// their B1 items, Polar primary items, Polar overflow items (one per Polar
-// stream with work) and status slots; one block-wide exclusive scan of the
-// four counts places them.  Then every thread writes the item table entries
-// of its streams: (stream, tile) for a B1 or primary item, (stream, -1 -
-// primary tiles) for an overflow item.  The table follows the tile status
-// words; its byte offset goes to the header (aux[2]).
-constexpr int kPrepThreads = 1024;
-constexpr int kPrepSums = 4;   // B1 items, Polar primary items, overflow items, slots
+// Three small kernels turn the descriptors into the item table:
+//   k_batched_count (a thread per stream) validates each descriptor and
+//     records its items and status slots (the 64-bit divisions and square
+//     roots, spread over the grid);
+//   k_batched_scan (one CTA) scans the four counts (B1 items, Polar primary
+//     items, Polar overflow items, slots) in stream order and places every
+//     stream: its status words, its first table entry, its overflow entry;
+//   k_batched_fill (a warp per stream) writes the stream's table entries:
+//     (stream, tile) for a B1 or primary item, (stream, -1 - primary tiles)
+//     for an overflow item.
+// The table follows the tile status words; its byte offset goes to the
+// header (aux[2]).  aux[3] collects the worst descriptor error.
+constexpr int kCountThreads = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kFillThreads = 256;
+constexpr int kScanSums = 4;   // B1 items, Polar primary items, overflow items, slots
 
-// The four counts of one descriptor (all 0 for an invalid one, which is
-// recorded in *bad).
-__device__ __forceinline__ void prep_counts(const nrng_stream_desc_t &d, int threads, int bpt, int *bad,
-                                            long long (&c)[kPrepSums])
+__global__ void __launch_bounds__(kCountThreads)
+k_batched_count(BatchedParams bp, int threads, int bpt)
 {
+    const int32_t j = blockIdx.x * kCountThreads + threadIdx.x;
+    if (j >= bp.k) return;
+    const nrng_stream_desc_t d = bp.desc[j];
     int64_t items, slots;
     stream_items(d, threads, bpt, items, slots);
-    c[0] = c[1] = c[2] = c[3] = 0;
+    BatchedCount c{0, 0, 0};
     if (items < 0) {
-        atomicMax(bad, items == -2 ? kStatusOverflow : kStatusInvalid);
-        return;
-    }
-    if (d.method == NRNG_B1) {
-        c[0] = items;
+        atomicMax(&bp.hdr->aux[3], (unsigned long long)(items == -2 ? kStatusOverflow : kStatusInvalid));
     } else if (items > 0) {
-        c[1] = items;
-        c[2] = 1;
-        c[3] = slots;
+        c.items = (int32_t)items;
+        c.polar = d.method == NRNG_POLAR ? 1 : 0;
+        c.slots = slots;
     }
+    bp.counts[j] = c;
 }
 
-__global__ void __launch_bounds__(kPrepThreads)
-k_batched_prep(BatchedParams bp, int threads, int bpt)
+// One 16-byte load of a stream's record.
+__device__ __forceinline__ BatchedCount load_count(const BatchedCount *p)
 {
-    __shared__ long long s_w[kPrepSums][kPrepThreads / 32];
-    __shared__ long long s_tot[kPrepSums];
-    __shared__ int s_bad;
+    const int4 r = *reinterpret_cast<const int4 *>(p);
+    return BatchedCount{r.x, r.y, (int64_t)(((uint64_t)(uint32_t)r.w << 32) | (uint32_t)r.z)};
+}
+
+__device__ __forceinline__ void scan_terms(const BatchedCount &c, long long (&v)[kScanSums])
+{
+    v[0] = c.polar ? 0 : c.items;
+    v[1] = c.polar ? c.items : 0;
+    v[2] = c.polar;
+    v[3] = c.slots;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_batched_scan(BatchedParams bp)
+{
+    __shared__ long long s_w[kScanSums][kScanThreads / 32];
+    __shared__ long long s_tot[kScanSums];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_bad = 0;
-    __syncthreads();
-    const int32_t per = (bp.k + kPrepThreads - 1) / kPrepThreads;
+    const int32_t per = (bp.k + kScanThreads - 1) / kScanThreads;
     const int32_t j0 = tid * per;
     const int32_t j1 = (j0 + per < bp.k) ? j0 + per : bp.k;
-    // Each descriptor's counts are computed once (64-bit divisions and a
-    // square root) and kept for the second pass when they fit here.
+    // The thread's first kKeep records are loaded at once and kept in
+    // registers for the second pass.
     constexpr int kKeep = 4;
-    long long keep[kKeep][kPrepSums];
-    long long m[kPrepSums] = {0, 0, 0, 0};
+    BatchedCount keep[kKeep];
 #pragma unroll
-    for (int r = 0; r < kKeep; ++r) {   // unrolled: the kept counts stay in registers
+    for (int r = 0; r < kKeep; ++r) keep[r] = (j0 + r < j1) ? load_count(bp.counts + j0 + r) : BatchedCount{0, 0, 0};
+    long long m[kScanSums] = {0, 0, 0, 0};
 #pragma unroll
-        for (int q = 0; q < kPrepSums; ++q) keep[r][q] = 0;
-        if (j0 + r < j1) prep_counts(bp.desc[j0 + r], threads, bpt, &s_bad, keep[r]);
+    for (int r = 0; r < kKeep; ++r) {
+        long long v[kScanSums];
+        scan_terms(keep[r], v);
 #pragma unroll
-        for (int q = 0; q < kPrepSums; ++q) m[q] += keep[r][q];
+        for (int q = 0; q < kScanSums; ++q) m[q] += v[q];
     }
-    for (int32_t j = j0 + kKeep; j < j1; ++j) {   // more than four descriptors a thread
-        long long c[kPrepSums];
-        prep_counts(bp.desc[j], threads, bpt, &s_bad, c);
+    for (int32_t j = j0 + kKeep; j < j1; ++j) {
+        long long v[kScanSums];
+        scan_terms(load_count(bp.counts + j), v);
 #pragma unroll
-        for (int q = 0; q < kPrepSums; ++q) m[q] += c[q];
+        for (int q = 0; q < kScanSums; ++q) m[q] += v[q];
     }
-    long long inc[kPrepSums];   // inclusive within the warp
+    long long inc[kScanSums];   // inclusive within the warp
 #pragma unroll
-    for (int q = 0; q < kPrepSums; ++q) inc[q] = m[q];
+    for (int q = 0; q < kScanSums; ++q) inc[q] = m[q];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
-        for (int q = 0; q < kPrepSums; ++q) {
+        for (int q = 0; q < kScanSums; ++q) {
             const long long a = __shfl_up_sync(0xFFFFFFFFu, inc[q], o);
             if (lane >= o) inc[q] += a;
         }
     }
     if (lane == 31)
 #pragma unroll
-        for (int q = 0; q < kPrepSums; ++q) s_w[q][warp] = inc[q];
+        for (int q = 0; q < kScanSums; ++q) s_w[q][warp] = inc[q];
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
-        for (int q = 0; q < kPrepSums; ++q) {
+        for (int q = 0; q < kScanSums; ++q) {
             long long v = s_w[q][lane];
             const long long v0 = v;
 #pragma unroll
@@ -227,40 +245,33 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
     }
     __syncthreads();
     const long long n_b1 = s_tot[0], n_pp = s_tot[1], n_po = s_tot[2], n_slots = s_tot[3];
-    const long long n_items = n_b1 + n_pp + n_po;
-    // the item table after the status words of every Polar stream; written
-    // only when the workspace holds it (else the status word reports it)
-    const size_t table_off = batched_layout(bp.k).tile_status + (size_t)n_slots * 8;
-    const bool table_fits = table_off + (size_t)n_items * 8 <= bp.ws_bytes;
-    int2 *table = reinterpret_cast<int2 *>(reinterpret_cast<char *>(bp.hdr) + table_off);
-    long long x[kPrepSums];   // exclusive for this thread
+    long long x[kScanSums];   // exclusive for this thread
 #pragma unroll
-    for (int q = 0; q < kPrepSums; ++q) x[q] = s_w[q][warp] + inc[q] - m[q];
+    for (int q = 0; q < kScanSums; ++q) x[q] = s_w[q][warp] + inc[q] - m[q];
     long long ib = x[0], ip = n_b1 + x[1], io = n_b1 + n_pp + x[2], cs = x[3];
-    auto place = [&](int32_t j, const long long (&c)[kPrepSums]) {
+    auto place = [&](int32_t j, const BatchedCount &c) {
         bp.slot_base[j] = cs;
-        if (table_fits) {
-            for (long long it = 0; it < c[0]; ++it) table[ib + it] = make_int2(j, (int)it);
-            for (long long it = 0; it < c[1]; ++it) table[ip + it] = make_int2(j, (int)it);
-            if (c[2]) table[io] = make_int2(j, -1 - (int)c[1]);
+        *reinterpret_cast<longlong2 *>(bp.item_base + 2 * j) = make_longlong2(c.polar ? ip : ib, c.polar ? io : -1);
+        if (c.polar) {
+            ip += c.items;
+            io += 1;
+        } else {
+            ib += c.items;
         }
-        ib += c[0];
-        ip += c[1];
-        io += c[2];
-        cs += c[3];
+        cs += c.slots;
     };
 #pragma unroll
     for (int r = 0; r < kKeep; ++r)
         if (j0 + r < j1) place(j0 + r, keep[r]);
-    for (int32_t j = j0 + kKeep; j < j1; ++j) {
-        long long c[kPrepSums];
-        int ignored = 0;   // recorded in the first pass
-        prep_counts(bp.desc[j], threads, bpt, &ignored, c);
-        place(j, c);
-    }
-    if (tid == kPrepThreads - 1) {
+    for (int32_t j = j0 + kKeep; j < j1; ++j) place(j, load_count(bp.counts + j));
+    if (tid == kScanThreads - 1) {
         bp.slot_base[bp.k] = cs;
-        int bad = s_bad;
+        // the item table after the status words of every Polar stream,
+        // written only when the workspace holds it
+        const long long n_items = n_b1 + n_pp + n_po;
+        const size_t table_off = batched_layout(bp.k).tile_status + (size_t)n_slots * 8;
+        const bool table_fits = table_off + (size_t)n_items * 8 <= bp.ws_bytes;
+        int bad = (int)bp.hdr->aux[3];
         if (!bad && !table_fits) bad = kStatusWorkspace;
         if (bad) {
             bp.hdr->status = bad;
@@ -273,6 +284,19 @@ k_batched_prep(BatchedParams bp, int threads, int bpt)
             bp.hdr->aux[2] = (unsigned long long)table_off;
         }
     }
+}
+
+__global__ void __launch_bounds__(kFillThreads)
+k_batched_fill(BatchedParams bp)
+{
+    const int32_t j = blockIdx.x * (kFillThreads / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= bp.k || bp.hdr->done) return;   // done: a descriptor or workspace error
+    int2 *table = reinterpret_cast<int2 *>(reinterpret_cast<char *>(bp.hdr) + bp.hdr->aux[2]);
+    const BatchedCount c = load_count(bp.counts + j);
+    const longlong2 base = *reinterpret_cast<const longlong2 *>(bp.item_base + 2 * j);
+    for (int32_t it = lane; it < c.items; it += 32) table[base.x + it] = make_int2(j, it);
+    if (c.polar && lane == 0) table[base.y] = make_int2(j, -1 - c.items);
 }
 
 // ------------------------------------------------------------ main --------
@@ -513,13 +537,20 @@ cudaError_t launch_batched(void *out, const nrng_stream_desc_t *desc, int32_t k,
     bp.hdr = reinterpret_cast<WsHeader *>(w);
     bp.slot_base = reinterpret_cast<int64_t *>(w + L.slot_base);
     bp.stream_done = reinterpret_cast<int *>(w + L.stream_done);
+    bp.counts = reinterpret_cast<BatchedCount *>(w + L.counts);
+    bp.item_base = reinterpret_cast<int64_t *>(w + L.item_base);
     bp.tile_status = reinterpret_cast<unsigned long long *>(w + L.tile_status);
     bp.ws_bytes = ws_bytes;
     bp.spin_limit_ns = spin_limit_ns();
     cudaError_t e = cudaMemsetAsync(ws, 0, ws_bytes, s);
     if (e != cudaSuccess) return e;
     const BatchedConfig c = kConfigs[config];
-    k_batched_prep<<<1, kPrepThreads, 0, s>>>(bp, c.threads, c.blocks_per_thread);
+    if (k > 0) {
+        k_batched_count<<<(k + kCountThreads - 1) / kCountThreads, kCountThreads, 0, s>>>(bp, c.threads,
+                                                                                        c.blocks_per_thread);
+        k_batched_scan<<<1, kScanThreads, 0, s>>>(bp);
+        k_batched_fill<<<(k + kFillThreads / 32 - 1) / (kFillThreads / 32), kFillThreads, 0, s>>>(bp);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (mode == kModeFast) return batched_dtype_dispatch<kModeFast>(bp, dtype, config, s);

@@ -69,11 +69,14 @@ struct PolarParams {
 // Largest n a Polar stream accepts (keeps the tile budget arithmetic exact).
 constexpr int64_t kPolarMaxN = int64_t(1) << 48;
 
-// floor(sqrt(v)) for 0 <= v < 2^62, exact: a double square root is within
-// one of the answer, and integer steps settle it.
+// floor(sqrt(v)) for 0 <= v < 2^62, exact: a float root (relative error
+// below 2^-22), one integer Newton step (then within one of the answer) and
+// integer steps that settle it.  No double arithmetic: the device's FP64
+// rate is a small fraction of its FP32 rate.
 __host__ __device__ inline int64_t isqrt64(int64_t v)
 {
-    int64_t r = (int64_t)sqrt((double)v);
+    int64_t r = (int64_t)sqrtf((float)v);
+    if (r > 0) r = (r + v / r) / 2;
     while (r > 0 && r * r > v) --r;
     while ((r + 1) * (r + 1) <= v) ++r;
     return r;
@@ -141,10 +144,18 @@ struct BatchedConfig {
 
 // Workspace of a batched call: header, then per-stream tables, then one tile
 // status word per Polar tile of every Polar stream, then the item table.
+struct BatchedCount {    // one stream's work, from its descriptor
+    int32_t items;       // B1 items, or Polar primary items
+    int32_t polar;       // 1 for a Polar stream with work (one overflow item)
+    int64_t slots;       // tile status words (a Polar stream's tile budget)
+};
+static_assert(sizeof(BatchedCount) == 16, "a stream's record is one 16-byte load");
 struct BatchedLayout {
     size_t slot_base;     // int64[k + 1]: first tile status word of each stream (the
                           // difference of neighbours: a Polar stream's tile budget)
     size_t stream_done;   // int32[k]: set once a Polar stream has all its pairs
+    size_t counts;        // BatchedCount[k]
+    size_t item_base;     // int64[2k]: a stream's first item-table entry, its overflow entry
     size_t tile_status;   // uint64[slots]
 };
 __host__ __device__ inline BatchedLayout batched_layout(int32_t k)
@@ -152,7 +163,9 @@ __host__ __device__ inline BatchedLayout batched_layout(int32_t k)
     BatchedLayout L;
     L.slot_base = sizeof(WsHeader);
     L.stream_done = L.slot_base + (size_t)(k + 1) * 8;
-    L.tile_status = (L.stream_done + (size_t)k * 4 + 255) / 256 * 256;
+    L.counts = (L.stream_done + (size_t)k * 4 + 15) / 16 * 16;
+    L.item_base = L.counts + (size_t)k * sizeof(BatchedCount);
+    L.tile_status = (L.item_base + (size_t)k * 16 + 255) / 256 * 256;
     return L;
 }
 
@@ -163,6 +176,8 @@ struct BatchedParams {
     WsHeader *hdr;
     int64_t *slot_base;
     int *stream_done;
+    BatchedCount *counts;
+    int64_t *item_base;
     unsigned long long *tile_status;
     size_t ws_bytes;
     unsigned long long spin_limit_ns;

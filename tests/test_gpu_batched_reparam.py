@@ -179,8 +179,9 @@ def test_batched_device_descriptor_errors():
     assert nr.nrng_get_status(ws) == nr._lib.ERR_INVALID_VALUE
     assert torch.equal(out, before)          # nothing written
     # a workspace large enough for the tables but not for the tile words
-    # (the tables of 8 streams take 256 bytes; the 4 Polar streams need >= 4 words)
-    small = torch.empty(264, dtype=torch.uint8, device="cuda")
+    # (the header and per-stream tables of 8 streams take 512 bytes; the 4
+    # Polar streams need >= 4 words)
+    small = torch.empty(520, dtype=torch.uint8, device="cuda")
     nr.nrng_batched(out, d_desc, len(desc), small, "accurate")
     assert nr.nrng_get_status(small) == nr._lib.ERR_WORKSPACE
     assert torch.equal(out, before)

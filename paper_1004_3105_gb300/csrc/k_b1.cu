@@ -7,6 +7,7 @@
 // The kernel is bound by the HBM write stream or by instruction dispatch
 // (Philox's 32x32->64 products and the transform), whichever is tighter.
 #include <algorithm>
+#include <atomic>
 
 #include "nrng_device.cuh"
 
@@ -81,8 +82,8 @@ k_b1_whole(T *__restrict__ out, int64_t n, uint32_t nwhole, float mu, float sigm
         const uint32_t lo = c_lo + b, lo2 = c_lo + b2;
         const uint32_t hi = CARRY ? c_hi + (lo < b ? 1u : 0u) : c_hi;
         const uint32_t hi2 = CARRY ? c_hi + (lo2 < b2 ? 1u : 0u) : c_hi;
-        const float4 o = b1_block<MODE>(philox4x32_10(lo, hi, rk), cf, tab);
-        const float4 o2 = b1_block<MODE>(philox4x32_10(lo2, hi2, rk), cf, tab);
+        float4 o, o2;
+        b1_block2<MODE>(philox4x32_10(lo, hi, rk), philox4x32_10(lo2, hi2, rk), cf, tab, o, o2);
         store4_aligned(out + 4 * (size_t)b, o.x, o.y, o.z, o.w);
         store4_aligned(out + 4 * (size_t)b2, o2.x, o2.y, o2.z, o2.w);
     }
@@ -158,41 +159,45 @@ cudaError_t launch_uniform(float *out, int64_t n, uint64_t key, uint64_t counter
 }
 
 template <int MODE, typename T>
-static void b1_dispatch_aligned(void *out, int64_t n, int64_t nblocks, float mu, float sigma,
+static cudaError_t b1_dispatch_aligned(void *out, int64_t n, int64_t nblocks, float mu, float sigma,
                                 uint64_t counter, const RoundKeys &rk, bool aligned, cudaStream_t s)
 {
+    // the whole-block kernel's grid: its resident CTAs on every SM (no
+    // partial second wave), grid-striding beyond
+    static std::atomic<int> occ_slot{0};
+    int occ = 0;
+    const cudaError_t e = cached_occupancy(occ_slot, k_b1_whole<MODE, T, false>, kB1Threads, occ);
+    if (e != cudaSuccess) return e;
+    const int grid_whole = (int)std::max<int64_t>(
+        1, std::min<int64_t>((nblocks + kB1Threads - 1) / kB1Threads, (int64_t)sm_count() * occ));
     const int grid = b1_grid(nblocks);
     const int64_t nwhole = n / 4;
     // the carry-free form when the low counter word does not wrap over the
     // launch (the whole blocks and the partial one)
     const bool carry_free = (uint64_t)(uint32_t)counter + (uint64_t)nblocks <= (uint64_t(1) << 32);
-    if (aligned && nwhole < (int64_t(1) << 32) - 2 * (int64_t)grid * kB1Threads && carry_free)
-        k_b1_whole<MODE, T, false><<<grid, kB1Threads, 0, s>>>((T *)out, n, (uint32_t)nwhole, mu, sigma,
-                                                                (uint32_t)counter, (uint32_t)(counter >> 32), rk);
-    else if (aligned && nwhole < (int64_t(1) << 32) - 2 * (int64_t)grid * kB1Threads)
-        k_b1_whole<MODE, T, true><<<grid, kB1Threads, 0, s>>>((T *)out, n, (uint32_t)nwhole, mu, sigma,
-                                                               (uint32_t)counter, (uint32_t)(counter >> 32), rk);
+    if (aligned && nwhole < (int64_t(1) << 32) - 2 * (int64_t)grid_whole * kB1Threads && carry_free)
+        k_b1_whole<MODE, T, false><<<grid_whole, kB1Threads, 0, s>>>((T *)out, n, (uint32_t)nwhole, mu, sigma,
+                                                                     (uint32_t)counter, (uint32_t)(counter >> 32), rk);
+    else if (aligned && nwhole < (int64_t(1) << 32) - 2 * (int64_t)grid_whole * kB1Threads)
+        k_b1_whole<MODE, T, true><<<grid_whole, kB1Threads, 0, s>>>((T *)out, n, (uint32_t)nwhole, mu, sigma,
+                                                                    (uint32_t)counter, (uint32_t)(counter >> 32), rk);
     else if (aligned)
         k_b1<MODE, T, true><<<grid, kB1Threads, 0, s>>>((T *)out, n, nblocks, mu, sigma, counter, rk);
     else
         k_b1<MODE, T, false><<<grid, kB1Threads, 0, s>>>((T *)out, n, nblocks, mu, sigma, counter, rk);
+    return cudaGetLastError();
 }
 
 template <int MODE>
-static void b1_dispatch_dtype(void *out, int64_t n, int64_t nblocks, float mu, float sigma,
-                              uint64_t counter, const RoundKeys &rk, int dtype, bool aligned,
-                              cudaStream_t s)
+static cudaError_t b1_dispatch_dtype(void *out, int64_t n, int64_t nblocks, float mu, float sigma,
+                                     uint64_t counter, const RoundKeys &rk, int dtype, bool aligned,
+                                     cudaStream_t s)
 {
     switch (dtype) {
-    case NRNG_F32:
-        b1_dispatch_aligned<MODE, float>(out, n, nblocks, mu, sigma, counter, rk, aligned, s);
-        break;
+    case NRNG_F32: return b1_dispatch_aligned<MODE, float>(out, n, nblocks, mu, sigma, counter, rk, aligned, s);
     case NRNG_BF16:
-        b1_dispatch_aligned<MODE, __nv_bfloat16>(out, n, nblocks, mu, sigma, counter, rk, aligned, s);
-        break;
-    default:
-        b1_dispatch_aligned<MODE, __half>(out, n, nblocks, mu, sigma, counter, rk, aligned, s);
-        break;
+        return b1_dispatch_aligned<MODE, __nv_bfloat16>(out, n, nblocks, mu, sigma, counter, rk, aligned, s);
+    default: return b1_dispatch_aligned<MODE, __half>(out, n, nblocks, mu, sigma, counter, rk, aligned, s);
     }
 }
 
@@ -201,13 +206,9 @@ cudaError_t launch_b1(void *out, int64_t n, float mu, float sigma, uint64_t key,
 {
     const int64_t nblocks = (n + 3) / 4;
     const RoundKeys rk = round_keys(key);
-    if (mode == kModeFast)
-        b1_dispatch_dtype<kModeFast>(out, n, nblocks, mu, sigma, counter, rk, dtype, aligned, s);
-    else if (mode == kModeB2)
-        b1_dispatch_dtype<kModeB2>(out, n, nblocks, mu, sigma, counter, rk, dtype, aligned, s);
-    else
-        b1_dispatch_dtype<kModeAccurate>(out, n, nblocks, mu, sigma, counter, rk, dtype, aligned, s);
-    return cudaGetLastError();
+    if (mode == kModeFast) return b1_dispatch_dtype<kModeFast>(out, n, nblocks, mu, sigma, counter, rk, dtype, aligned, s);
+    if (mode == kModeB2) return b1_dispatch_dtype<kModeB2>(out, n, nblocks, mu, sigma, counter, rk, dtype, aligned, s);
+    return b1_dispatch_dtype<kModeAccurate>(out, n, nblocks, mu, sigma, counter, rk, dtype, aligned, s);
 }
 
 }  // namespace nrng

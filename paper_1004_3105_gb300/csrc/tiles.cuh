@@ -26,8 +26,8 @@ __device__ __forceinline__ void b1_tile(T *__restrict__ out, int64_t n, const Ra
         T *o = out + 4 * b00;
         uint32_t lo = lo00;
         for (int r = 0; r < BPT; r += 2, lo += 2 * THREADS, o += 8 * THREADS) {
-            const float4 v = b1_block<MODE>(philox4x32_10(lo, hi00, rk), cf, tab);
-            const float4 v2 = b1_block<MODE>(philox4x32_10(lo + THREADS, hi00, rk), cf, tab);
+            float4 v, v2;
+            b1_block2<MODE>(philox4x32_10(lo, hi00, rk), philox4x32_10(lo + THREADS, hi00, rk), cf, tab, v, v2);
             store4_aligned(o, v.x, v.y, v.z, v.w);
             store4_aligned(o + 4 * THREADS, v2.x, v2.y, v2.z, v2.w);
         }
@@ -47,8 +47,8 @@ __device__ __forceinline__ void b1_tile(T *__restrict__ out, int64_t n, const Ra
                 w = philox4x32_10(lo00 + (uint32_t)(r * THREADS), hi00, rk);
                 w2 = philox4x32_10(lo00 + (uint32_t)((r + 1) * THREADS), hi00, rk);
             }
-            const float4 o = b1_block<MODE>(w, cf, tab);
-            const float4 o2 = b1_block<MODE>(w2, cf, tab);
+            float4 o, o2;
+            b1_block2<MODE>(w, w2, cf, tab, o, o2);
             store4_aligned(out + 4 * b, o.x, o.y, o.z, o.w);
             store4_aligned(out + 4 * b2, o2.x, o2.y, o2.z, o2.w);
             continue;

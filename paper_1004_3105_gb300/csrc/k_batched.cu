@@ -45,7 +45,7 @@ namespace nrng {
 // measured 9% faster on the 4096-stream workload than 128 x 8 although shared
 // memory then holds six CTAs per SM (512-thread tiles were never faster).
 static const BatchedConfig kConfigs[] = {
-    {128, 16}, {128, 12}, {128, 8}, {256, 8}, {128, 4}, {256, 4},
+    {128, 18}, {128, 16}, {128, 12}, {128, 8}, {256, 8}, {128, 4}, {256, 4},
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
@@ -506,11 +506,12 @@ template <int MODE, typename T>
 static cudaError_t batched_config_dispatch(const BatchedParams &bp, int config, cudaStream_t s)
 {
     switch (config) {
-    case 0: return batched_main<128, 16, MODE, T>(bp, s);
-    case 1: return batched_main<128, 12, MODE, T>(bp, s);
-    case 2: return batched_main<128, 8, MODE, T>(bp, s);
-    case 3: return batched_main<256, 8, MODE, T>(bp, s);
-    case 4: return batched_main<128, 4, MODE, T>(bp, s);
+    case 0: return batched_main<128, 18, MODE, T>(bp, s);
+    case 1: return batched_main<128, 16, MODE, T>(bp, s);
+    case 2: return batched_main<128, 12, MODE, T>(bp, s);
+    case 3: return batched_main<128, 8, MODE, T>(bp, s);
+    case 4: return batched_main<256, 8, MODE, T>(bp, s);
+    case 5: return batched_main<128, 4, MODE, T>(bp, s);
     default: return batched_main<256, 4, MODE, T>(bp, s);
     }
 }

@@ -67,7 +67,7 @@ template <class Policy, typename T>
 static cudaError_t reject_launch_t(const PolarParams &p, bool aligned, cudaStream_t s)
 {
     static std::atomic<int> occ_a{0}, occ_p{0};
-    const bool cf = reject_carry_free(p.counter, p.tiles_max);
+    const bool cf = reject_carry_free(p.counter, p.tiles_max, kPolarThreads * Policy::kRows);
     auto kern = aligned ? (cf ? k_reject<Policy, T, true, false> : k_reject<Policy, T, true, true>)
                         : (cf ? k_reject<Policy, T, false, false> : k_reject<Policy, T, false, true>);
     int occ = 0;
@@ -97,7 +97,7 @@ cudaError_t launch_polar_p2(const PolarParams &p, int dtype, bool aligned, cudaS
 
 int64_t ratio_tiles_max(int64_t n)
 {
-    return ratio_tiles_for(n, kPolarCandPerTile);
+    return ratio_tiles_for(n, kRatioCandPerTile);
 }
 
 size_t ratio_workspace_bytes(int64_t n)

@@ -34,7 +34,7 @@ template <int MODE, typename T>
 static cudaError_t polar_launch_t(const PolarParams &p, bool aligned, cudaStream_t s)
 {
     static std::atomic<int> occ_aligned{0}, occ_plain{0};
-    const bool cf = reject_carry_free(p.counter, p.tiles_max);
+    const bool cf = reject_carry_free(p.counter, p.tiles_max, kPolarBlocksPerTile);
     auto kern = aligned ? (cf ? k_reject<PolarPolicy<MODE>, T, true, false> : k_reject<PolarPolicy<MODE>, T, true, true>)
                         : (cf ? k_reject<PolarPolicy<MODE>, T, false, false> : k_reject<PolarPolicy<MODE>, T, false, true>);
     int occ = 0;
@@ -140,10 +140,10 @@ k_polar_scan(const int *__restrict__ counts, long long *__restrict__ prefix, int
 }
 
 template <int MODE, typename T, bool ALIGNED>
-__global__ void __launch_bounds__(kPolarThreads, (RejOccupancy<kRejWarps, kRejRows>::kMinBlocks))
+__global__ void __launch_bounds__(kPolarThreads, (RejOccupancy<kRejWarps, kPolarRows>::kMinBlocks))
 k_polar_write(const PolarParams p, const long long *__restrict__ prefix)
 {
-    __shared__ RejSmem<kRejWarps, kRejRows> sm;
+    __shared__ RejSmem<kRejWarps, kPolarRows> sm;
     const RadiusCoef cf = radius_coef(p.mu, p.sigma);
     PolarStream ps;
     ps.n = p.n;
@@ -160,7 +160,7 @@ k_polar_write(const PolarParams p, const long long *__restrict__ prefix)
     for (int64_t t = blockIdx.x; t < p.tiles_max; t += gridDim.x) {
         const long long P = prefix[t];   // same value for every thread of the CTA
         if (P >= p.nitems) break;        // prefixes only grow with t
-        reject_tile<PolarPolicy<MODE>, kRejWarps, kRejRows, T, ALIGNED, true, RoundKeys, true>(sm, out, ps, p.rk, cf, t,
+        reject_tile<PolarPolicy<MODE>, kRejWarps, kPolarRows, T, ALIGNED, true, RoundKeys, true>(sm, out, ps, p.rk, cf, t,
                                                                                             p.hdr, p.spin_limit_ns, P);
         __syncthreads();
     }

@@ -384,13 +384,14 @@ int32_t nrng_boxmuller_b3(void *d_out, int64_t n, float mu, float sigma, uint64_
 // Shared checks and parameters of the single-stream rejection calls (P2, R).
 static int32_t reject_params(PolarParams &p, void *d_out, int64_t n, int64_t nitems, float mu, float sigma,
                              uint64_t key, uint64_t counter, int32_t dtype, void *d_ws, size_t ws_bytes,
-                             size_t ws_need, int64_t tiles, uint64_t *d_next_counter, int64_t *d_cand)
+                             size_t ws_need, int64_t tiles, int blocks_per_tile, uint64_t *d_next_counter,
+                             int64_t *d_cand)
 {
     if ((uintptr_t)d_out % dtype_size(dtype) || (uintptr_t)d_ws % 8 || (uintptr_t)d_next_counter % 8 ||
         (uintptr_t)d_cand % 8)
         return NRNG_ERR_MISALIGNED;
     if (d_ws == nullptr || ws_bytes < ws_need) return NRNG_ERR_WORKSPACE;
-    if (!counter_fits(counter, (uint64_t)tiles * kPolarBlocksPerTile)) return NRNG_ERR_COUNTER_OVERFLOW;
+    if (!counter_fits(counter, (uint64_t)tiles * blocks_per_tile)) return NRNG_ERR_COUNTER_OVERFLOW;
     p.out = d_out;
     p.n = n;
     p.nitems = nitems;
@@ -425,8 +426,8 @@ int32_t nrng_polar_p2(void *d_out, int64_t n, float mu, float sigma, uint64_t ke
     }
     PolarParams p;
     const int32_t st = reject_params(p, d_out, n, (n + 1) / 2, mu, sigma, key, counter, dtype, d_ws, ws_bytes,
-                                     polar_workspace_bytes(n), polar_tiles_max(n), d_next_counter,
-                                     d_pair_candidate);
+                                     polar_workspace_bytes(n), polar_tiles_max(n), kPolarBlocksPerTile,
+                                     d_next_counter, d_pair_candidate);
     if (st != NRNG_OK) return st;
     const bool aligned = ((uintptr_t)d_out % (2 * dtype_size(dtype))) == 0;
     return cuda_status(launch_polar_p2(p, dtype, aligned, (cudaStream_t)stream), "nrng_polar_p2");
@@ -455,7 +456,8 @@ int32_t nrng_ratio(void *d_out, int64_t n, float mu, float sigma, uint64_t key, 
     }
     PolarParams p;
     const int32_t st = reject_params(p, d_out, n, n, mu, sigma, key, counter, dtype, d_ws, ws_bytes,
-                                     ratio_workspace_bytes(n), ratio_tiles_max(n), d_next_counter, d_candidate);
+                                     ratio_workspace_bytes(n), ratio_tiles_max(n), kRatioBlocksPerTile,
+                                     d_next_counter, d_candidate);
     if (st != NRNG_OK) return st;
     const bool aligned = ((uintptr_t)d_out % (2 * dtype_size(dtype))) == 0;
     return cuda_status(launch_ratio(p, dtype, mode, aligned, (cudaStream_t)stream), "nrng_ratio");

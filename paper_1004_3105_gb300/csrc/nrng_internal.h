@@ -41,14 +41,17 @@ struct WsHeader {
 static_assert(sizeof(WsHeader) == 64, "workspace header is 64 bytes");
 
 // ---------------------------------------------------------------- Polar --
-// Tile of the single-stream rejection kernels (Algorithm P, Method P2,
-// Algorithm R): kRejWarps warps x kRejRows rows x 32 lanes x 2 candidates.
+// Tiles of the single-stream rejection kernels: kRejWarps warps x rows x 32
+// lanes x 2 candidates, 18 rows for Algorithm P and Method P2 and 14 for
+// Algorithm R (measured best for each; at 18 rows six CTAs still fit per SM).
 constexpr int kRejWarps = 4;
-constexpr int kRejRows = 16;
 constexpr int kPolarThreads = kRejWarps * 32;                   // 128
-constexpr int kPolarRows = kRejRows;                            // Philox blocks per thread per tile
-constexpr int kPolarBlocksPerTile = kPolarThreads * kPolarRows; // 2048
-constexpr int kPolarCandPerTile = 2 * kPolarBlocksPerTile;      // 4096
+constexpr int kPolarRows = 18;                                  // Philox blocks per thread per tile
+constexpr int kRatioRows = 14;
+constexpr int kPolarBlocksPerTile = kPolarThreads * kPolarRows; // 2304
+constexpr int kPolarCandPerTile = 2 * kPolarBlocksPerTile;      // 4608
+constexpr int kRatioBlocksPerTile = kPolarThreads * kRatioRows; // 1792
+constexpr int kRatioCandPerTile = 2 * kRatioBlocksPerTile;      // 3584
 
 struct PolarParams {
     void *out;

@@ -160,6 +160,7 @@ __device__ __forceinline__ void store_item_bits(T *p, int2 v)
 template <int MODE>
 struct PolarPolicy {
     static constexpr int kOut = 2;
+    static constexpr int kRows = kPolarRows;   // rows of the single-stream tile
     __device__ static bool accept(uint32_t wa, uint32_t wb, int2 &pay) { return polar_accept_scaled(wa, wb, pay); }
     __device__ static void transform(int2 p, const RadiusCoef &c, float &a, float &b)
     {
@@ -170,6 +171,7 @@ struct PolarPolicy {
 // Method P2 (Sec. 4): Algorithm P's steps 1-3, step 4a.
 struct P2Policy {
     static constexpr int kOut = 2;
+    static constexpr int kRows = kPolarRows;
     __device__ static bool accept(uint32_t wa, uint32_t wb, int2 &pay) { return polar_accept_scaled(wa, wb, pay); }
     __device__ static void transform(int2 p, const RadiusCoef &c, float &a, float &b)
     {
@@ -181,6 +183,7 @@ struct P2Policy {
 template <int MODE>
 struct RatioPolicy {
     static constexpr int kOut = 1;
+    static constexpr int kRows = kRatioRows;
     __device__ static bool accept(uint32_t wu, uint32_t wv, int2 &pay) { return ratio_accept(wu, wv, pay); }
     __device__ static void transform(int2 p, const RadiusCoef &c, float &a, float &b)
     {
@@ -413,10 +416,10 @@ struct RejOccupancy {
 // from the workspace counter until the stream is complete (done) or the tile
 // budget is spent.
 template <class Policy, typename T, bool ALIGNED, bool CARRY>
-__global__ void __launch_bounds__(kRejWarps * 32, (RejOccupancy<kRejWarps, kRejRows>::kMinBlocks))
+__global__ void __launch_bounds__(kRejWarps * 32, (RejOccupancy<kRejWarps, Policy::kRows>::kMinBlocks))
 k_reject(const PolarParams p)
 {
-    __shared__ RejSmem<kRejWarps, kRejRows> sm;
+    __shared__ RejSmem<kRejWarps, Policy::kRows> sm;
     PolarStream ps;
     ps.n = p.n;
     ps.nitems = p.nitems;
@@ -434,8 +437,8 @@ k_reject(const PolarParams p)
         __syncthreads();
         const long long t = sm.tile;
         if (t < 0) break;
-        const bool ok = reject_tile<Policy, kRejWarps, kRejRows, T, ALIGNED, CARRY>(sm, out, ps, p.rk, cf, t, p.hdr,
-                                                                                 p.spin_limit_ns);
+        const bool ok = reject_tile<Policy, kRejWarps, Policy::kRows, T, ALIGNED, CARRY>(sm, out, ps, p.rk, cf, t,
+                                                                                      p.hdr, p.spin_limit_ns);
         __syncthreads();
         if (!ok) break;
     }
@@ -443,9 +446,9 @@ k_reject(const PolarParams p)
 
 // Whether the low counter word of every Philox block of a rejection stream's
 // tile budget stays below 2^32 (the kernels' carry-free form).
-__host__ __device__ inline bool reject_carry_free(uint64_t counter, int64_t tiles_max)
+__host__ __device__ inline bool reject_carry_free(uint64_t counter, int64_t tiles_max, int blocks_per_tile)
 {
-    return (uint64_t)(uint32_t)counter + (uint64_t)tiles_max * (uint64_t)kPolarBlocksPerTile <= (uint64_t(1) << 32);
+    return (uint64_t)(uint32_t)counter + (uint64_t)tiles_max * (uint64_t)blocks_per_tile <= (uint64_t(1) << 32);
 }
 
 }  // namespace nrng

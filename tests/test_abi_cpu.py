@@ -76,13 +76,14 @@ def test_polar_workspace_and_validation(lib):
     assert lib.nrng_polar_workspace_size(-1, ctypes.byref(b)) == _lib.ERR_INVALID_VALUE
     assert lib.nrng_polar_workspace_size(1 << 28, ctypes.byref(b)) == _lib.OK
     ws = b.value
-    # one 8-byte word per tile of 4096 candidates at the 0.78 budget + 64-byte header
+    # one 8-byte word per tile of 4608 candidates (4 warps x 18 rows x 32 lanes
+    # x 2) at the 0.78 budget + 64-byte header
     tiles = ((1 << 27) + 12 * (int(np.sqrt(1 << 27)) + 1) + 16) * 100
-    tiles = (tiles + 4096 * 78 - 1) // (4096 * 78) + 1
+    tiles = (tiles + 4608 * 78 - 1) // (4608 * 78) + 1
     assert ws == (64 + 8 * tiles + 255) // 256 * 256
     blocks = ctypes.c_uint64(0)
     assert lib.nrng_polar_max_blocks(1 << 28, ctypes.byref(blocks)) == _lib.OK
-    assert blocks.value == tiles * 2048
+    assert blocks.value == tiles * 2304
     # workspace too small / missing
     f = lib.nrng_polar
     assert f(FAKE, 100, 0.0, 1.0, 1, 0, 0, 0, FAKE, 8, None, None, None) == _lib.ERR_WORKSPACE
@@ -125,9 +126,10 @@ def test_ratio_workspace_and_validation(lib):
     assert lib.nrng_ratio_workspace_size(-1, ctypes.byref(b)) == _lib.ERR_INVALID_VALUE
     n = 1 << 28
     assert lib.nrng_ratio_workspace_size(n, ctypes.byref(b)) == _lib.OK
-    # one word per tile of 4096 candidates at the 0.72 budget (acceptance sqrt(pi e)/4 = 0.7306)
+    # one word per tile of 3584 candidates (4 warps x 14 rows x 32 lanes x 2)
+    # at the 0.72 budget (acceptance sqrt(pi e)/4 = 0.7306)
     tiles = (n + 12 * (int(np.sqrt(n)) + 1) + 16) * 100
-    tiles = (tiles + 4096 * 72 - 1) // (4096 * 72) + 1
+    tiles = (tiles + 3584 * 72 - 1) // (3584 * 72) + 1
     assert b.value == (64 + 8 * tiles + 255) // 256 * 256
     f = lib.nrng_ratio
     assert f(FAKE, 100, 0.0, 1.0, 1, 0, 0, 0, FAKE, 8, None, None, None) == _lib.ERR_WORKSPACE
@@ -167,7 +169,7 @@ def test_batched_workspace_size(lib):
     # items its expected tiles at acceptance pi/4 plus one overflow item; a B1
     # stream has no slots and one item per four tiles
     worst = 0
-    for threads, bpt in [(128, 16), (128, 12), (128, 8), (256, 8), (128, 4), (256, 4)]:
+    for threads, bpt in [(128, 18), (128, 16), (128, 12), (128, 8), (256, 8), (128, 4), (256, 4)]:
         cand = 2 * threads * bpt
         s = 0
         for n, m in zip([100, 1000, 0, 5000], [0, 1, 1, 1]):
@@ -232,20 +234,20 @@ def test_reparam_validation(lib):
 
 def test_config_table(lib):
     n = lib.nrng_batched_config_count()
-    assert n == 6
+    assert n == 7
     t, b = ctypes.c_int32(0), ctypes.c_int32(0)
     seen = set()
     for c in range(n):
         assert lib.nrng_batched_config_info(c, ctypes.byref(t), ctypes.byref(b)) == _lib.OK
         seen.add((t.value, b.value))
-        assert t.value % 32 == 0 and 2 * t.value * b.value <= 4096
+        assert t.value % 32 == 0 and b.value % 2 == 0 and 2 * t.value * b.value <= 4608
     assert len(seen) == n
     assert lib.nrng_batched_config_info(n, ctypes.byref(t), ctypes.byref(b)) == _lib.ERR_INVALID_VALUE
     c = ctypes.c_int32(0)
     assert lib.nrng_batched_set_config(0, 1, 4) == _lib.OK
     assert lib.nrng_batched_get_config(0, 1, ctypes.byref(c)) == _lib.OK and c.value == 4
     assert lib.nrng_batched_set_config(0, 1, -1) == _lib.OK
-    assert lib.nrng_batched_get_config(0, 1, ctypes.byref(c)) == _lib.OK and c.value == 0   # default 128 x 16
+    assert lib.nrng_batched_get_config(0, 1, ctypes.byref(c)) == _lib.OK and c.value == 0   # default 128 x 18
     assert lib.nrng_batched_set_config(0, 1, 99) == _lib.ERR_INVALID_VALUE
 
 

@@ -39,11 +39,12 @@ namespace nrng {
 // ------------------------------------------------------------ configs -----
 // (threads per CTA, Philox blocks per thread per tile).  A Polar tile stages
 // at most 64 accepted points per warp and row, 8 bytes each, in shared
-// memory, plus 8 bytes of accept ballots per (row, warp): 33.6 KB for 128 x 16
-// or 256 x 8.  Long tiles of 128 threads are the default: the per-item claim
-// and the per-tile scan and look-back are spread over more candidates, which
-// measured 9% faster on the 4096-stream workload than 128 x 8 although shared
-// memory then holds six CTAs per SM (512-thread tiles were never faster).
+// memory, plus 8 bytes of accept ballots per (row, warp): 37.5 KB for 128 x 18,
+// 33.6 KB for 128 x 16 or 256 x 8.  Long tiles of 128 threads are the default:
+// the per-item claim and the per-tile scan and look-back are spread over more
+// candidates (128 x 16 measured 9% faster on the 4096-stream workload than
+// 128 x 8, and 128 x 18, the longest tile at which six CTAs still fit per SM,
+// 1.4% faster than 128 x 16; 512-thread tiles were never faster).
 static const BatchedConfig kConfigs[] = {
     {128, 18}, {128, 16}, {128, 12}, {128, 8}, {256, 8}, {128, 4}, {256, 4},
 };

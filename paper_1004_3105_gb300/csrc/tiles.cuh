@@ -261,11 +261,10 @@ __device__ __forceinline__ bool reject_tile(RejSmem<NW, R> &sm, T *__restrict__ 
         const uint32_t lo0 = (uint32_t)c0, hi0 = (uint32_t)(c0 >> 32);
         int2 *seg = sm.seg[warp];
         int base = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t lo = lo0 + (uint32_t)(r * 32);
-            const uint32_t hi = CARRY ? hi0 + (lo < lo0 ? 1u : 0u) : hi0;
-            const uint4 w = philox4x32_10(lo, hi, rk);
+        // Two rows per step: their Philox chains are independent and fill each
+        // other's multiply latencies.
+        static_assert(R % 2 == 0, "rows are drawn in pairs");
+        auto row = [&](int r, const uint4 &w) {
             int2 p0, p1;
             const bool a0 = Policy::accept(w.x, w.y, p0);
             const bool a1 = Policy::accept(w.z, w.w, p1);
@@ -276,6 +275,16 @@ __device__ __forceinline__ bool reject_tile(RejSmem<NW, R> &sm, T *__restrict__ 
             if (a1) seg[pos + (a0 ? 1 : 0)] = p1;
             if (lane == 0) sm.mask[warp][r] = make_uint2(m0, m1);
             base += __popc(m0) + __popc(m1);
+        };
+#pragma unroll
+        for (int r = 0; r < R; r += 2) {
+            const uint32_t lo = lo0 + (uint32_t)(r * 32), lo2 = lo + 32u;
+            const uint32_t hi = CARRY ? hi0 + (lo < lo0 ? 1u : 0u) : hi0;
+            const uint32_t hi2 = CARRY ? hi0 + (lo2 < lo0 ? 1u : 0u) : hi0;
+            const uint4 w = philox4x32_10(lo, hi, rk);
+            const uint4 w2 = philox4x32_10(lo2, hi2, rk);
+            row(r, w);
+            row(r + 1, w2);
         }
         if (lane == 0) sm.cnt[warp] = base;
     }

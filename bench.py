@@ -297,8 +297,8 @@ class Step:
         # n/pi per Polar stream
         self.batch_philox_blocks = float(sum(int(n) / 4 if m == 0 else int(n) / math.pi
                                              for n, m in zip(wl.n, wl.method)))
-        # our kernels per step: B1 1, Polar 1, batched 4 (count, scan, fill, main), reparam fwd + bwd 2
-        self.our_launches_per_step = 8
+        # our kernels per step: B1 1, Polar 1, batched 3 (count, fill, main), reparam fwd + bwd 2
+        self.our_launches_per_step = 7
 
     def part_b1(self):
         self.nr.nrng_boxmuller(self.out_b1, 0.0, 1.0, KEY, self.base, "accurate")

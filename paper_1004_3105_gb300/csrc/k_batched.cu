@@ -4,9 +4,9 @@
 // The paper amortises the cost of a call by returning whole arrays (Sec. 3)
 // and buffers the variable output of its vector Polar kernel (Sec. 4,
 // RANN3/RANN3B).  Here thousands of uneven streams share one grid:
-//   k_batched_count, k_batched_scan and k_batched_fill validate the
-//     descriptors, turn each stream into work items and write the item table
-//     (a thread, one CTA and a warp per stream): first every B1 stream's items
+//   k_batched_count and k_batched_fill validate the descriptors, turn each
+//     stream into work items (a thread per stream, one scan across the grid)
+//     and write the item table (a warp per stream): first every B1 stream's items
 //     (runs of its tiles), then every Polar stream's primary items (its
 //     expected number of tiles, one item each), then one overflow item per
 //     Polar stream that runs whatever tiles the stream still needs, one after
@@ -135,41 +135,22 @@ size_t batched_workspace_bytes(const nrng_stream_desc_t *h_desc, int32_t k)
 }
 
 // ------------------------------------------------------------ prep --------
-// Three small kernels turn the descriptors into the item table:
-//   k_batched_count (a thread per stream) validates each descriptor and
-//     records its items and status slots (the 64-bit divisions and square
-//     roots, spread over the grid);
-//   k_batched_scan (one CTA) scans the four counts (B1 items, Polar primary
-//     items, Polar overflow items, slots) in stream order and places every
-//     stream: its status words, its first table entry, its overflow entry;
+// Two small kernels turn the descriptors into the item table:
+//   k_batched_count (a thread per stream, kSetupThreads streams a CTA)
+//     validates each descriptor, counts its B1 items, Polar primary items,
+//     Polar overflow items (one per Polar stream with work) and status slots,
+//     and places the stream with one scan over all streams: a block scan, then
+//     a decoupled look-back across CTAs (taken in ticket order, so a CTA only
+//     waits on CTAs that have started) for each of the four counts and for a
+//     fifth, the descriptor errors.  The CTA with the last ticket has the
+//     totals and writes them to the header;
 //   k_batched_fill (a warp per stream) writes the stream's table entries:
 //     (stream, tile) for a B1 or primary item, (stream, -1 - primary tiles)
-//     for an overflow item.
-// The table follows the tile status words; its byte offset goes to the
-// header (aux[2]).  aux[3] collects the worst descriptor error.
-constexpr int kCountThreads = 256;
-constexpr int kScanThreads = 1024;
+//     for an overflow item.  The table follows the tile status words: B1
+//     items, then Polar primary items, then overflow items.
+// Header: aux[0] items, aux[1] B1 items, aux[2] the table's byte offset,
+// aux[3] the first overflow item, aux[4] the setup's CTA tickets.
 constexpr int kFillThreads = 256;
-constexpr int kScanSums = 4;   // B1 items, Polar primary items, overflow items, slots
-
-__global__ void __launch_bounds__(kCountThreads)
-k_batched_count(BatchedParams bp, int threads, int bpt)
-{
-    const int32_t j = blockIdx.x * kCountThreads + threadIdx.x;
-    if (j >= bp.k) return;
-    const nrng_stream_desc_t d = bp.desc[j];
-    int64_t items, slots;
-    stream_items(d, threads, bpt, items, slots);
-    BatchedCount c{0, 0, 0};
-    if (items < 0) {
-        atomicMax(&bp.hdr->aux[3], (unsigned long long)(items == -2 ? kStatusOverflow : kStatusInvalid));
-    } else if (items > 0) {
-        c.items = (int32_t)items;
-        c.polar = d.method == NRNG_POLAR ? 1 : 0;
-        c.slots = slots;
-    }
-    bp.counts[j] = c;
-}
 
 // One 16-byte load of a stream's record.
 __device__ __forceinline__ BatchedCount load_count(const BatchedCount *p)
@@ -178,101 +159,175 @@ __device__ __forceinline__ BatchedCount load_count(const BatchedCount *p)
     return BatchedCount{r.x, r.y, (int64_t)(((uint64_t)(uint32_t)r.w << 32) | (uint32_t)r.z)};
 }
 
-__device__ __forceinline__ void scan_terms(const BatchedCount &c, long long (&v)[kScanSums])
+// Decoupled look-back of warp 0 over NQ quantities at once: status word
+// status[q stride + c] holds CTA c's quantity q (aggregate or inclusive
+// prefix flag, as the tiles' status words).  Each poll reads 32 predecessors'
+// NQ words (one per lane and quantity) and each quantity sums back to its own
+// nearest prefix, so one round trip serves all NQ.  Returns false when the
+// wait ran out (the error is recorded); every wait is bounded as in
+// lookback_warp.
+template <int NQ>
+__device__ __forceinline__ bool lookback_multi(unsigned long long *status, long long stride, long long c,
+                                               const long long (&agg)[NQ], long long (&excl)[NQ], WsHeader *hdr,
+                                               unsigned long long limit_ns)
 {
-    v[0] = c.polar ? 0 : c.items;
-    v[1] = c.polar ? c.items : 0;
-    v[2] = c.polar;
-    v[3] = c.slots;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) excl[q] = 0;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            st_relaxed(status + q * stride + c, (c == 0 ? kFlagPrefix : kFlagAggregate) | (unsigned long long)agg[q]);
+    if (c == 0) return true;
+    bool found[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) found[q] = false;
+    long long base = c - 1;
+    unsigned long long t0 = 0;
+    unsigned polls = 0;
+    for (;;) {
+        const long long idx = base - lane;
+        unsigned long long w[NQ];
+        unsigned pre[NQ], nr[NQ], win[NQ];
+        bool wait = false;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            w[q] = (idx >= 0 && !found[q]) ? ld_relaxed(status + q * stride + idx) : kFlagPrefix;
+            pre[q] = __ballot_sync(0xFFFFFFFFu, (unsigned)(w[q] >> 62) == 2u);
+            nr[q] = __ballot_sync(0xFFFFFFFFu, (unsigned)(w[q] >> 62) == 0u);
+            const unsigned lm = pre[q] & (0u - pre[q]);   // the nearest prefix (pre[q] != 0 once found)
+            win[q] = pre[q] ? (lm | (lm - 1u)) : 0xFFFFFFFFu;
+            wait |= (nr[q] & win[q]) != 0u;
+        }
+        if (wait) {
+            if (polls == 0) t0 = global_timer_ns();
+            ++polls;
+            bool give_up = (polls >= (1u << 24)) || (global_timer_ns() - t0 > limit_ns) ||
+                           (ld_relaxed_s32(&hdr->status) != 0);
+            give_up = __shfl_sync(0xFFFFFFFFu, give_up, 0);
+            if (give_up) {
+                if (lane == 0 && ld_relaxed_s32(&hdr->status) == 0) raise_error(hdr, kStatusTimeout);
+                return false;
+            }
+            __nanosleep(polls < 4 ? 64u : 256u);
+            continue;
+        }
+        bool all = true;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            if (found[q]) continue;
+            long long v = ((win[q] >> lane) & 1u) ? (long long)(w[q] & kValueMask) : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            excl[q] += v;
+            found[q] = pre[q] != 0u;
+            all = all && found[q];
+        }
+        if (all) break;
+        base -= 32;
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) st_relaxed(status + q * stride + c, kFlagPrefix | (unsigned long long)(excl[q] + agg[q]));
+    return true;
 }
 
-__global__ void __launch_bounds__(kScanThreads)
-k_batched_scan(BatchedParams bp)
+// Errors, summed over the streams without carrying between the two kinds:
+// counter overflows in the high half, invalid descriptors in the low half.
+constexpr int kErrShift = 31;
+
+__global__ void __launch_bounds__(kSetupThreads)
+k_batched_count(BatchedParams bp, int threads, int bpt)
 {
-    __shared__ long long s_w[kScanSums][kScanThreads / 32];
-    __shared__ long long s_tot[kScanSums];
+    __shared__ long long s_w[kSetupSums][kSetupThreads / 32];
+    __shared__ long long s_x[kSetupSums];
+    __shared__ long long s_ticket;
+    __shared__ int s_ok;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int32_t per = (bp.k + kScanThreads - 1) / kScanThreads;
-    const int32_t j0 = tid * per;
-    const int32_t j1 = (j0 + per < bp.k) ? j0 + per : bp.k;
-    // The thread's first kKeep records are loaded at once and kept in
-    // registers for the second pass.
-    constexpr int kKeep = 4;
-    BatchedCount keep[kKeep];
-#pragma unroll
-    for (int r = 0; r < kKeep; ++r) keep[r] = (j0 + r < j1) ? load_count(bp.counts + j0 + r) : BatchedCount{0, 0, 0};
-    long long m[kScanSums] = {0, 0, 0, 0};
-#pragma unroll
-    for (int r = 0; r < kKeep; ++r) {
-        long long v[kScanSums];
-        scan_terms(keep[r], v);
-#pragma unroll
-        for (int q = 0; q < kScanSums; ++q) m[q] += v[q];
+    if (tid == 0) s_ticket = (long long)atomicAdd(&bp.hdr->aux[4], 1ull);
+    __syncthreads();
+    const long long c = s_ticket;
+    const long long nctas = ((long long)bp.k + kSetupThreads - 1) / kSetupThreads;
+    const long long jl = c * kSetupThreads + tid;
+    const int32_t j = (int32_t)jl;
+    long long v[kSetupSums] = {0, 0, 0, 0, 0};
+    BatchedCount rec{0, 0, 0};
+    if (jl < bp.k) {
+        const nrng_stream_desc_t d = bp.desc[j];
+        int64_t items, slots;
+        stream_items(d, threads, bpt, items, slots);
+        if (items < 0) {
+            v[4] = (items == -2) ? (1ll << kErrShift) : 1ll;
+        } else if (items > 0) {
+            rec.items = (int32_t)items;
+            rec.polar = d.method == NRNG_POLAR ? 1 : 0;
+            rec.slots = slots;
+            v[rec.polar ? 1 : 0] = items;
+            v[2] = rec.polar;
+            v[3] = slots;
+        }
+        bp.counts[j] = rec;
     }
-    for (int32_t j = j0 + kKeep; j < j1; ++j) {
-        long long v[kScanSums];
-        scan_terms(load_count(bp.counts + j), v);
+    // block scan of the five quantities
+    long long inc[kSetupSums];
 #pragma unroll
-        for (int q = 0; q < kScanSums; ++q) m[q] += v[q];
-    }
-    long long inc[kScanSums];   // inclusive within the warp
-#pragma unroll
-    for (int q = 0; q < kScanSums; ++q) inc[q] = m[q];
+    for (int q = 0; q < kSetupSums; ++q) inc[q] = v[q];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
-        for (int q = 0; q < kScanSums; ++q) {
-            const long long a = __shfl_up_sync(0xFFFFFFFFu, inc[q], o);
-            if (lane >= o) inc[q] += a;
+        for (int q = 0; q < kSetupSums; ++q) {
+            const long long y = __shfl_up_sync(0xFFFFFFFFu, inc[q], o);
+            if (lane >= o) inc[q] += y;
         }
     }
     if (lane == 31)
 #pragma unroll
-        for (int q = 0; q < kScanSums; ++q) s_w[q][warp] = inc[q];
+        for (int q = 0; q < kSetupSums; ++q) s_w[q][warp] = inc[q];
     __syncthreads();
     if (warp == 0) {
+        long long agg[kSetupSums];
 #pragma unroll
-        for (int q = 0; q < kScanSums; ++q) {
-            long long v = s_w[q][lane];
-            const long long v0 = v;
+        for (int q = 0; q < kSetupSums; ++q) {
+            long long y = lane < kSetupThreads / 32 ? s_w[q][lane] : 0;
+            const long long y0 = y;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long a = __shfl_up_sync(0xFFFFFFFFu, v, o);
-                if (lane >= o) v += a;
+            for (int o = 1; o < kSetupThreads / 32; o <<= 1) {
+                const long long z = __shfl_up_sync(0xFFFFFFFFu, y, o);
+                if (lane >= o) y += z;
             }
-            s_w[q][lane] = v - v0;   // exclusive warp offsets
-            if (lane == 31) s_tot[q] = v;
+            if (lane < kSetupThreads / 32) s_w[q][lane] = y - y0;   // exclusive warp offsets
+            agg[q] = __shfl_sync(0xFFFFFFFFu, y, kSetupThreads / 32 - 1);
+        }
+        // the CTA's place among all streams: one look-back for the five
+        long long P[kSetupSums];
+        const bool ok = lookback_multi<kSetupSums>(bp.setup_status, nctas, c, agg, P, bp.hdr, bp.spin_limit_ns);
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < kSetupSums; ++q) s_x[q] = P[q];
+            s_ok = ok ? 1 : 0;
         }
     }
     __syncthreads();
-    const long long n_b1 = s_tot[0], n_pp = s_tot[1], n_po = s_tot[2], n_slots = s_tot[3];
-    long long x[kScanSums];   // exclusive for this thread
+    if (!s_ok) return;   // a look-back gave up: the error is recorded
+    long long x[kSetupSums];   // exclusive prefixes of this thread's stream
 #pragma unroll
-    for (int q = 0; q < kScanSums; ++q) x[q] = s_w[q][warp] + inc[q] - m[q];
-    long long ib = x[0], ip = n_b1 + x[1], io = n_b1 + n_pp + x[2], cs = x[3];
-    auto place = [&](int32_t j, const BatchedCount &c) {
-        bp.slot_base[j] = cs;
-        *reinterpret_cast<longlong2 *>(bp.item_base + 2 * j) = make_longlong2(c.polar ? ip : ib, c.polar ? io : -1);
-        if (c.polar) {
-            ip += c.items;
-            io += 1;
-        } else {
-            ib += c.items;
-        }
-        cs += c.slots;
-    };
-#pragma unroll
-    for (int r = 0; r < kKeep; ++r)
-        if (j0 + r < j1) place(j0 + r, keep[r]);
-    for (int32_t j = j0 + kKeep; j < j1; ++j) place(j, load_count(bp.counts + j));
-    if (tid == kScanThreads - 1) {
-        bp.slot_base[bp.k] = cs;
+    for (int q = 0; q < kSetupSums; ++q) x[q] = s_x[q] + s_w[q][warp] + inc[q] - v[q];
+    if (jl < bp.k) {
+        bp.slot_base[j] = x[3];
+        *reinterpret_cast<longlong2 *>(bp.item_base + 2 * jl) =
+            make_longlong2(rec.polar ? x[1] : x[0], rec.polar ? x[2] : -1);
+    }
+    if (c == nctas - 1 && tid == kSetupThreads - 1) {
+        // the last CTA's last thread: the totals
+        const long long n_b1 = x[0] + v[0], n_pp = x[1] + v[1], n_po = x[2] + v[2], n_slots = x[3] + v[3];
+        const long long errs = x[4] + v[4];
+        const long long n_items = n_b1 + n_pp + n_po;
+        bp.slot_base[bp.k] = n_slots;
         // the item table after the status words of every Polar stream,
         // written only when the workspace holds it
-        const long long n_items = n_b1 + n_pp + n_po;
         const size_t table_off = batched_layout(bp.k).tile_status + (size_t)n_slots * 8;
         const bool table_fits = table_off + (size_t)n_items * 8 <= bp.ws_bytes;
-        int bad = (int)bp.hdr->aux[3];
+        int bad = (errs >> kErrShift) ? kStatusOverflow : (errs ? kStatusInvalid : 0);
         if (!bad && !table_fits) bad = kStatusWorkspace;
         if (bad) {
             bp.hdr->status = bad;
@@ -283,6 +338,7 @@ k_batched_scan(BatchedParams bp)
             bp.hdr->aux[0] = (unsigned long long)n_items;
             bp.hdr->aux[1] = (unsigned long long)n_b1;
             bp.hdr->aux[2] = (unsigned long long)table_off;
+            bp.hdr->aux[3] = (unsigned long long)(n_b1 + n_pp);
         }
     }
 }
@@ -292,12 +348,14 @@ k_batched_fill(BatchedParams bp)
 {
     const int32_t j = blockIdx.x * (kFillThreads / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (j >= bp.k || bp.hdr->done) return;   // done: a descriptor or workspace error
+    if (j >= bp.k || bp.hdr->done) return;   // done: a descriptor, workspace or setup error
     int2 *table = reinterpret_cast<int2 *>(reinterpret_cast<char *>(bp.hdr) + bp.hdr->aux[2]);
     const BatchedCount c = load_count(bp.counts + j);
     const longlong2 base = *reinterpret_cast<const longlong2 *>(bp.item_base + 2 * j);
-    for (int32_t it = lane; it < c.items; it += 32) table[base.x + it] = make_int2(j, it);
-    if (c.polar && lane == 0) table[base.y] = make_int2(j, -1 - c.items);
+    // B1 items first, then the Polar primary items, then the overflow items
+    const long long first = c.polar ? (long long)bp.hdr->aux[1] + base.x : base.x;
+    for (int32_t it = lane; it < c.items; it += 32) table[first + it] = make_int2(j, it);
+    if (c.polar && lane == 0) table[(long long)bp.hdr->aux[3] + base.y] = make_int2(j, -1 - c.items);
 }
 
 // ------------------------------------------------------------ main --------
@@ -541,6 +599,7 @@ cudaError_t launch_batched(void *out, const nrng_stream_desc_t *desc, int32_t k,
     bp.stream_done = reinterpret_cast<int *>(w + L.stream_done);
     bp.counts = reinterpret_cast<BatchedCount *>(w + L.counts);
     bp.item_base = reinterpret_cast<int64_t *>(w + L.item_base);
+    bp.setup_status = reinterpret_cast<unsigned long long *>(w + L.setup_status);
     bp.tile_status = reinterpret_cast<unsigned long long *>(w + L.tile_status);
     bp.ws_bytes = ws_bytes;
     bp.spin_limit_ns = spin_limit_ns();
@@ -548,9 +607,8 @@ cudaError_t launch_batched(void *out, const nrng_stream_desc_t *desc, int32_t k,
     if (e != cudaSuccess) return e;
     const BatchedConfig c = kConfigs[config];
     if (k > 0) {
-        k_batched_count<<<(k + kCountThreads - 1) / kCountThreads, kCountThreads, 0, s>>>(bp, c.threads,
+        k_batched_count<<<(k + kSetupThreads - 1) / kSetupThreads, kSetupThreads, 0, s>>>(bp, c.threads,
                                                                                         c.blocks_per_thread);
-        k_batched_scan<<<1, kScanThreads, 0, s>>>(bp);
         k_batched_fill<<<(k + kFillThreads / 32 - 1) / (kFillThreads / 32), kFillThreads, 0, s>>>(bp);
     }
     e = cudaGetLastError();

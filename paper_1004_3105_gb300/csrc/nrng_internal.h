@@ -153,22 +153,28 @@ struct BatchedCount {    // one stream's work, from its descriptor
     int64_t slots;       // tile status words (a Polar stream's tile budget)
 };
 static_assert(sizeof(BatchedCount) == 16, "a stream's record is one 16-byte load");
+constexpr int kSetupThreads = 256;   // streams per CTA of the batched setup
+constexpr int kSetupSums = 5;        // its look-back quantities (see k_batched.cu)
 struct BatchedLayout {
     size_t slot_base;     // int64[k + 1]: first tile status word of each stream (the
                           // difference of neighbours: a Polar stream's tile budget)
     size_t stream_done;   // int32[k]: set once a Polar stream has all its pairs
     size_t counts;        // BatchedCount[k]
-    size_t item_base;     // int64[2k]: a stream's first item-table entry, its overflow entry
+    size_t item_base;     // int64[2k]: a stream's first item-table entry, its overflow
+                          // entry, each counted within its part of the table
+    size_t setup_status;  // uint64[kSetupSums x setup CTAs]: the setup's look-back words
     size_t tile_status;   // uint64[slots]
 };
 __host__ __device__ inline BatchedLayout batched_layout(int32_t k)
 {
     BatchedLayout L;
+    const size_t ctas = ((size_t)k + kSetupThreads - 1) / kSetupThreads;
     L.slot_base = sizeof(WsHeader);
     L.stream_done = L.slot_base + (size_t)(k + 1) * 8;
     L.counts = (L.stream_done + (size_t)k * 4 + 15) / 16 * 16;
     L.item_base = L.counts + (size_t)k * sizeof(BatchedCount);
-    L.tile_status = (L.item_base + (size_t)k * 16 + 255) / 256 * 256;
+    L.setup_status = L.item_base + (size_t)k * 16;
+    L.tile_status = (L.setup_status + ctas * kSetupSums * 8 + 255) / 256 * 256;
     return L;
 }
 
@@ -181,6 +187,7 @@ struct BatchedParams {
     int *stream_done;
     BatchedCount *counts;
     int64_t *item_base;
+    unsigned long long *setup_status;
     unsigned long long *tile_status;
     size_t ws_bytes;
     unsigned long long spin_limit_ns;

@@ -161,9 +161,10 @@ def test_batched_workspace_size(lib):
     assert lib.nrng_batched_workspace_size(d.ctypes.data_as(ctypes.c_void_p), len(d), ctypes.byref(b)) == _lib.OK
     k = len(d)
     # header, slot bases (k + 1), completion flags, per-stream counts and
-    # item bases (16 bytes each, from a 16-byte boundary), then 256-aligned
+    # item bases (16 bytes each, from a 16-byte boundary), the setup's five
+    # look-back words per 256 streams, then 256-aligned
     counts = (64 + (k + 1) * 8 + k * 4 + 15) // 16 * 16
-    fixed = (counts + 16 * k + 16 * k + 255) // 256 * 256
+    fixed = (counts + 16 * k + 16 * k + 5 * 8 * ((k + 255) // 256) + 255) // 256 * 256
     # most status slots plus item-table entries over the configurations (one
     # 8-byte entry each): a Polar stream's slots are its tile budget and its
     # items its expected tiles at acceptance pi/4 plus one overflow item; a B1

@@ -522,6 +522,11 @@ k_batched(BatchedParams bp)
             ps.pair_cand = nullptr;
             ps.silent_tile = -1;
             const bool aligned = ((uintptr_t)out % (2 * sizeof(T))) == 0;
+            // candidates a short stream's tile 0 is expected to need,
+            // nitems / (pi/4): its first draw takes the warps that reach into
+            // them (whole warps, so mostly with room to spare), and a second
+            // draw the rest when they fall short
+            const int limit0 = (ps.nitems < kCand) ? (int)((float)ps.nitems * 1.2732395f) : kCand;
             for (long long t = t0; t < t1; ++t) {
                 if (t > t0) {
                     // overflow item: stop once the stream is complete
@@ -536,10 +541,12 @@ k_batched(BatchedParams bp)
                     if (threadIdx.x == 0) st_relaxed(ps.status + t, kFlagPrefix | (unsigned long long)ps.nitems);
                 } else if (aligned) {
                     ok = reject_tile<PolarPolicy<MODE>, THREADS / 32, BPT, T, true, true, RoundKeys, false>(
-                        sm.rej, out, ps, rk, cf, t, bp.hdr, bp.spin_limit_ns, 0, ClaimAhead{&bp.hdr->tile_counter, &ahead, !overflow});
+                        sm.rej, out, ps, rk, cf, t, bp.hdr, bp.spin_limit_ns, 0,
+                        ClaimAhead{&bp.hdr->tile_counter, &ahead, !overflow}, t == 0 ? limit0 : kCand);
                 } else {
                     ok = reject_tile<PolarPolicy<MODE>, THREADS / 32, BPT, T, false, true, RoundKeys, false>(
-                        sm.rej, out, ps, rk, cf, t, bp.hdr, bp.spin_limit_ns, 0, ClaimAhead{&bp.hdr->tile_counter, &ahead, !overflow});
+                        sm.rej, out, ps, rk, cf, t, bp.hdr, bp.spin_limit_ns, 0,
+                        ClaimAhead{&bp.hdr->tile_counter, &ahead, !overflow}, t == 0 ? limit0 : kCand);
                 }
                 __syncthreads();
                 if (!ok) break;

@@ -87,6 +87,7 @@ struct RejSmem {
     int cnt[NW];            // accepted candidates of each warp
     int off[NW];            // exclusive offsets of the warps within the tile
     int total;              // accepted candidates of the tile
+    int drawn;              // accepted candidates of a limited tile 0's first draw
     long long prefix;       // the tile's exclusive prefix (-1 after an error)
     long long tile;         // the claimed tile id (single-stream kernels)
 };
@@ -236,7 +237,10 @@ __device__ __forceinline__ int tile_candidate(const RejSmem<NW, R> &sm, int warp
 // scan): nothing is published and nothing is awaited.  With CARRY false the
 // low counter word of the tile's blocks does not wrap (the caller checks).
 // on_prefix() runs on thread 0 once the tile's prefix is known (after the
-// look-back, before the copy-out), when the look-back succeeded.
+// look-back, before the copy-out), when the look-back succeeded.  cand_limit,
+// for tile 0 only (its prefix is 0), is the number of candidates the stream
+// is expected to need: a tile 0 that holds more draws only the warps that
+// reach into the limit, and the others only if those fall short.
 struct NoPrefixHook {
     __device__ void operator()() const {}
 };
@@ -246,7 +250,7 @@ template <class Policy, int NW, int R, typename T, bool ALIGNED, bool CARRY, typ
 __device__ __forceinline__ bool reject_tile(RejSmem<NW, R> &sm, T *__restrict__ out, const PolarStream &ps,
                                             const Key &rk, const RadiusCoef &cf, int64_t t, WsHeader *hdr,
                                             unsigned long long limit_ns, long long known_prefix = 0,
-                                            OnPrefix on_prefix = OnPrefix())
+                                            OnPrefix on_prefix = OnPrefix(), int cand_limit = 1 << 30)
 {
     constexpr int kBPT = NW * R * 32;   // Philox blocks of a tile
     constexpr int kCand = 2 * kBPT;
@@ -256,7 +260,7 @@ __device__ __forceinline__ bool reject_tile(RejSmem<NW, R> &sm, T *__restrict__ 
     const unsigned lt = (1u << lane) - 1u;
 
     // A: steps 1-3, compacted per warp.
-    {
+    auto draw = [&]() {
         const uint64_t c0 = ps.counter + (uint64_t)t * kBPT + (uint64_t)(warp * R * 32 + lane);
         const uint32_t lo0 = (uint32_t)c0, hi0 = (uint32_t)(c0 >> 32);
         int2 *seg = sm.seg[warp];
@@ -287,8 +291,33 @@ __device__ __forceinline__ bool reject_tile(RejSmem<NW, R> &sm, T *__restrict__ 
             row(r + 1, w2);
         }
         if (lane == 0) sm.cnt[warp] = base;
+    };
+    if (cand_limit >= kCand) {
+        draw();
+        __syncthreads();
+    } else {
+        // Tile 0 of a stream that is expected to need fewer candidates than a
+        // tile holds (cand_limit): the warps whose candidates all lie beyond
+        // the limit draw nothing at first.  The drawn warps are a prefix
+        // of the tile's candidates, so if they hold the stream's nitems accepted
+        // candidates the tile's output is the full tile's; otherwise the other
+        // warps draw theirs too.  (CTA-uniform: every thread sees the same t
+        // and limit.)
+        const bool first = warp * R * 64 < cand_limit;
+        if (first) draw();
+        else if (lane == 0) sm.cnt[warp] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int drawn = 0;
+            for (int q = 0; q < NW; ++q) drawn += sm.cnt[q];
+            sm.drawn = drawn;
+        }
+        __syncthreads();
+        if (sm.drawn < ps.nitems) {
+            if (!first) draw();
+            __syncthreads();
+        }
     }
-    __syncthreads();
 
     // B: warp 0 scans the warp counts and publishes the aggregate.
     int total = 0;

@@ -40,7 +40,7 @@ def check_batch(wl, out, mode, what):
         assert np.all(got.float().cpu().numpy()[mask] == sentinel)
 
 
-@pytest.mark.parametrize("config", range(6))
+@pytest.mark.parametrize("config", range(7))
 def test_batched_every_config(config):
     wl, desc, d_desc, out, ws = make_batch(64, 1, 20000, "mixed", align=1)
     nr.nrng_batched_set_config(torch.float32, "accurate", config)
@@ -189,6 +189,53 @@ def test_batched_device_descriptor_errors():
     nr.nrng_batched(out, d_desc, len(desc), ws, "accurate")
     assert nr.nrng_get_status(ws) == 0
     check_batch(wl, out, "accurate", "after errors")
+
+
+def test_batched_short_stream_tile0_second_draw():
+    """A Polar stream shorter than a tile draws, in its tile 0, only the warps
+    that reach into the candidates it is expected to need (nitems / (pi/4)),
+    and the other warps only when those fall short.  Streams whose expected
+    need sits just below a warp boundary (1152 candidates a warp in the
+    default 128 x 18 configuration) are picked with the oracle's accept bits
+    so that both cases occur: some fall short and take the second draw, some
+    do not.  Every stream must match the oracle and, bit for bit, the
+    single-stream kernel."""
+    per_warp = 18 * 64
+    picked, short, enough = [], 0, 0
+    for key in range(1, 2000):
+        if short >= 6 and enough >= 6:
+            break
+        for nitems in (900, 904, 1808, 1809):
+            limit = int(np.float32(nitems) * np.float32(1.2732395))
+            warps = -(-limit // per_warp)
+            acc, _, _ = oracle.polar_candidates(warps * per_warp, key, 0, coords=False)
+            falls_short = int(acc.sum()) < nitems
+            if (falls_short and short < 6) or (not falls_short and enough < 6):
+                picked.append((key, 2 * nitems))
+                short += falls_short
+                enough += not falls_short
+    assert short >= 6 and enough >= 6
+    n = np.array([m for _, m in picked], dtype=np.int64)
+    offset = np.concatenate([[0], np.cumsum(n)[:-1]]).astype(np.int64)
+    k = len(n)
+    mu, sigma = np.full(k, 0.5, np.float32), np.full(k, 1.5, np.float32)
+    key = np.array([q for q, _ in picked], dtype=np.uint64)
+    desc = nr.stream_descriptors(offset, n, mu, sigma, key, np.zeros(k, np.uint64), np.ones(k, np.int32))
+    total = int(n.sum())
+    out = torch.full((total,), -12345.0, dtype=torch.float32, device="cuda")
+    ws = torch.empty(nr.nrng_batched_workspace_size(desc), dtype=torch.uint8, device="cuda")
+    nr.nrng_batched_set_config(torch.float32, "accurate", 0)
+    nr.nrng_batched(out, nr.descriptors_to_device(desc), k, ws, "accurate")
+    assert nr.nrng_get_status(ws) == 0
+    got = out.cpu()
+    for j in range(k):
+        o, m = int(offset[j]), int(n[j])
+        ref, _, _, _ = oracle.polar(m, 0.5, 1.5, int(key[j]), 0)
+        assert_close(got[o:o + m].cuda(), ref, 0.5, 1.5, "accurate", f"short stream {j} (key {int(key[j])}, n {m})")
+        one = torch.empty(m, dtype=torch.float32, device="cuda")
+        wsp = nr.polar_workspace(m)
+        nr.nrng_polar(one, 0.5, 1.5, int(key[j]), 0, wsp, "accurate")
+        assert torch.equal(one.cpu(), got[o:o + m]), f"short stream {j}: batched differs from nrng_polar"
 
 
 # ------------------------------------------------------------------ reparam

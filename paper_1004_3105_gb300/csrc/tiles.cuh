@@ -427,14 +427,17 @@ __device__ __forceinline__ bool reject_tile(RejSmem<NW, R> &sm, T *__restrict__ 
     return true;
 }
 
-// Next tile id of a single rejection stream, or -1 once the stream is
-// complete or the tile budget is spent.
-// The completion flag is read before the claim, never alongside it: a tile
-// claimed and then dropped would never publish, and a later tile's look-back
-// would wait on it until its limit.
-__device__ __forceinline__ long long claim_tile(const PolarParams &p)
+// Next tile id of a single rejection stream, or -1 once the tile budget is
+// spent; *late is set when the stream was already complete.  The completion
+// flag and the claim are issued together (one round trip).  A tile claimed
+// after completion is never dropped unpublished (a later tile's look-back
+// would wait on it until its limit): the caller publishes it as complete.
+// That is exact: a claim that sees the flag set comes after the tile holding
+// the last item, whose look-back had to see every earlier tile published, so
+// the claimed tile's prefix is at least nitems.
+__device__ __forceinline__ long long claim_tile(const PolarParams &p, int &late)
 {
-    if (ld_relaxed_s32(&p.hdr->done) != 0) return -1;
+    late = ld_relaxed_s32(&p.hdr->done);
     const long long t = (long long)atomicAdd(&p.hdr->tile_counter, 1ull);
     return t < p.tiles_max ? t : -1;
 }
@@ -471,7 +474,16 @@ k_reject(const PolarParams p)
     const RadiusCoef cf = radius_coef(p.mu, p.sigma);
     T *out = static_cast<T *>(p.out);
     for (;;) {
-        if (threadIdx.x == 0) sm.tile = claim_tile(p);
+        if (threadIdx.x == 0) {
+            int late;
+            long long t = claim_tile(p, late);
+            if (t >= 0 && late) {
+                // the stream is complete: every later tile's prefix is >= nitems
+                if (t != ps.silent_tile) st_relaxed(ps.status + t, kFlagPrefix | (unsigned long long)ps.nitems);
+                t = -1;
+            }
+            sm.tile = t;
+        }
         __syncthreads();
         const long long t = sm.tile;
         if (t < 0) break;

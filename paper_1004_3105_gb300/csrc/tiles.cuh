@@ -167,6 +167,10 @@ struct PolarPolicy {
     {
         polar_pair<MODE>(p.x, p.y, c, a, b);
     }
+    __device__ static void transform2(int2 p, int2 q, const RadiusCoef &c, float &a, float &b, float &d, float &e)
+    {
+        polar_pair2<MODE>(p, q, c, a, b, d, e);
+    }
 };
 
 // Method P2 (Sec. 4): Algorithm P's steps 1-3, step 4a.
@@ -177,6 +181,11 @@ struct P2Policy {
     __device__ static void transform(int2 p, const RadiusCoef &c, float &a, float &b)
     {
         p2_pair(p.x >> 8, p.y >> 8, c.mu, c.sigma, a, b);   // exact: multiples of 2^8
+    }
+    __device__ static void transform2(int2 p, int2 q, const RadiusCoef &c, float &a, float &b, float &d, float &e)
+    {
+        transform(p, c, a, b);
+        transform(q, c, d, e);
     }
 };
 
@@ -190,6 +199,11 @@ struct RatioPolicy {
     {
         a = ratio_value<MODE>(p, c.mu, c.sigma);
         b = 0.0f;
+    }
+    __device__ static void transform2(int2 p, int2 q, const RadiusCoef &c, float &a, float &b, float &d, float &e)
+    {
+        transform(p, c, a, b);
+        transform(q, c, d, e);
     }
 };
 
@@ -345,8 +359,7 @@ __device__ __forceinline__ bool reject_tile(RejSmem<NW, R> &sm, T *__restrict__ 
         int2 *const end = sm.seg[warp] + sm.cnt[warp];
         for (; q + 32 < end; q += 64) {
             float za, zb, zc, zd;
-            Policy::transform(q[0], cf, za, zb);
-            Policy::transform(q[32], cf, zc, zd);
+            Policy::transform2(q[0], q[32], cf, za, zb, zc, zd);
             q[0] = (K == 2) ? pair_bits<T>(za, zb) : item_bits<T>(za);
             q[32] = (K == 2) ? pair_bits<T>(zc, zd) : item_bits<T>(zc);
         }

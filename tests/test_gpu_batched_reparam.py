@@ -191,6 +191,18 @@ def test_batched_device_descriptor_errors():
     check_batch(wl, out, "accurate", "after errors")
 
 
+def test_batched_many_streams_setup_lookback():
+    """20,000 short streams: the setup places them with a block scan per 256
+    streams and a look-back across 79 CTAs, more than its 32-wide window
+    covers, so a CTA whose nearer predecessors have not yet published their
+    prefixes walks back over several windows.  Every stream must match the
+    oracle."""
+    wl, desc, d_desc, out, ws = make_batch(20000, 1, 64, "mixed", align=1)
+    nr.nrng_batched(out, d_desc, len(desc), ws, "accurate")
+    assert nr.nrng_get_status(ws) == 0
+    check_batch(wl, out, "accurate", "20000 streams")
+
+
 def test_batched_short_stream_tile0_second_draw():
     """A Polar stream shorter than a tile draws, in its tile 0, only the warps
     that reach into the candidates it is expected to need (nitems / (pi/4)),

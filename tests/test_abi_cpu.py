@@ -97,6 +97,28 @@ def test_polar_workspace_and_validation(lib):
         _lib.ERR_INVALID_VALUE
 
 
+def test_tile_budget_integer_sqrt(lib):
+    """The tile budget takes floor(sqrt(items)) in integers (a float root, one
+    Newton step and exact corrections): around perfect squares, where a root
+    one off would change the budget, the workspace sizes must follow the
+    exact integer square root (items = ceil(n/2) for P, n for R)."""
+    import math
+    b = ctypes.c_size_t(0)
+    ks = [1, 2, 3, 1000, 46340, 46341, 65535, 65536, 1 << 20, (1 << 23) - 1, 1 << 23, 3037000499 >> 8]
+    for k in ks:
+        for items in (k * k - 1, k * k, k * k + 1):
+            if items < 1:
+                continue
+            n = 2 * items   # P: ceil(n/2) = items
+            assert lib.nrng_polar_workspace_size(n, ctypes.byref(b)) == _lib.OK
+            need = items + 12 * (math.isqrt(items) + 1) + 16
+            tiles = (need * 100 + 4608 * 78 - 1) // (4608 * 78) + 1
+            assert b.value == (64 + 8 * tiles + 255) // 256 * 256, (n, b.value)
+            assert lib.nrng_ratio_workspace_size(items, ctypes.byref(b)) == _lib.OK
+            tiles = (need * 100 + 3584 * 72 - 1) // (3584 * 72) + 1
+            assert b.value == (64 + 8 * tiles + 255) // 256 * 256, (items, b.value)
+
+
 def test_b3_validation(lib):
     f = lib.nrng_boxmuller_b3
     assert f(None, 5, 0.0, 1.0, 1, 0, 0, None) == _lib.ERR_INVALID_VALUE

@@ -103,9 +103,9 @@ def test_polar_accurate_radius():
     """ln s of the accurate Polar path at every S = k^2 (0 < k < 2^23, so s
     runs from 2^-46 to 1 - 2^-22) and at 4 M random lattice points: the
     radius |(x, y) - mu| = sigma sqrt(-2 ln s) against the oracle.  Below
-    1 - s = 2^-7 the path takes a series in the exact complement; above it
+    1 - s = 2^-8 the path takes a series in the exact complement; above it
     the hardware log2 of s (s rounded to 2^-23), whose error moves the radius
-    by under 1.4e-6 absolute at 1 - s = 2^-7 and less beyond.  A coordinate's
+    most near 1 - s = 2^-8 (measured 9.3e-7) and less beyond.  A coordinate's
     error from the radius is at most the radius error and |z| <= r, so the
     radius is held to half the accurate bound, 2e-6 max(1, r)."""
     k = np.arange(1, 1 << 23, dtype=np.int64)

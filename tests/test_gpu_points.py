@@ -54,7 +54,7 @@ def test_b1_accurate_every_lattice_radius_and_angle():
     values, at t = 0, where sin = 0 and cos = 1 exactly, so y = r) and every
     angle t (2^24 values, at u = 1 - e^-1/2, where r is near 1), against the
     oracle.  The radius takes the hardware log2 of the exact 1 - u above
-    u = 2^-8 (its absolute error moves r by under 4e-7 there, less beyond)
+    u = 2^-9 (its absolute error moves r most there: measured 7.9e-7)
     and a three-term series below it.  A coordinate's error from the radius is
     at most the radius error and |z| <= r, so the radius is held to half the
     accurate bound, 2e-6 max(1, r).  The angle comes from the 1024-entry table
